@@ -1,0 +1,222 @@
+"""Seeded synthetic inputs for the tridiagonal-to-band eigenvector back-transform.
+
+This module is shared by the CPU oracle tests and the GPU path. It only draws
+random numbers and lays them out; it holds none of the method's arithmetic
+(no bulge chasing, no eigensolve, no reflector application).
+
+Random numbers come from a counter-based splitmix64 stream: element ``i`` of
+stream ``s`` under seed ``seed`` is ``splitmix64(mix(seed, s) + (i+1)*phi)``,
+``u = (x >> 11) * 2**-53`` in [0, 1), normals by the Box-Muller cosine branch.
+Counter-based draws make every array reproducible independently of the others
+and of the order they are generated in.
+
+Workloads (the paper's random / KS-DFT-like problems, Sec. 4 and Sec. 5; the
+paper does not state a distribution, so these are this library's choice):
+
+* ``uniform`` band: lower band including the diagonal i.i.d. U[-1, 1],
+  mirrored to a symmetric matrix.
+* ``dft`` band: diagonal U[-10, 10] sorted ascending, sub-diagonals
+  ``d = 1..b`` drawn N(0, 1) * exp(-d/16) (real and imaginary part each for
+  Hermitian problems), mirrored (conjugated) to a symmetric/Hermitian matrix.
+
+Band matrices are returned in lower band storage ``W[d, c] = B[c+d, c]`` of
+shape ``(b+1, n)``; entries with ``c + d >= n`` are zero.
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+PHI = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+# Seed of workload ``k`` (1-based, in the order listed in the design notes).
+SEED_BASE = 2002109910
+
+
+def _mix(z: np.ndarray) -> np.ndarray:
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
+def _stream_key(seed: int, stream: int) -> np.uint64:
+    with np.errstate(over="ignore"):
+        k = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) ^ (np.uint64(stream & 0xFFFFFFFF) * _M2)
+        return _mix(np.array([k], dtype=np.uint64))[0]
+
+
+def splitmix64(seed: int, stream: int, count: int, offset: int = 0) -> np.ndarray:
+    """``count`` 64-bit words of stream ``stream`` starting at counter ``offset``."""
+    key = _stream_key(seed, stream)
+    idx = np.arange(offset + 1, offset + count + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        return _mix(key + idx * PHI)
+
+
+def uniform(seed: int, stream: int, shape, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
+    n = int(np.prod(shape)) if len(shape) else 1
+    u = (splitmix64(seed, stream, n) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    return (lo + (hi - lo) * u).reshape(shape)
+
+
+def normal(seed: int, stream: int, shape) -> np.ndarray:
+    n = int(np.prod(shape)) if len(shape) else 1
+    w = splitmix64(seed, stream, 2 * n)
+    u1 = (w[0::2] >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    u2 = (w[1::2] >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    z = np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * math.pi * u2)
+    return z.reshape(shape)
+
+
+# ----------------------------------------------------------------------------
+# band matrices (the input of the band -> tridiagonal reduction, Eq. 6b)
+# ----------------------------------------------------------------------------
+
+def band_uniform(n: int, b: int, seed: int, complex_: bool = False) -> np.ndarray:
+    """Lower band (incl. diagonal) i.i.d. U[-1,1]; Hermitian input gets a real diagonal."""
+    W = uniform(seed, 1, (b + 1, n), -1.0, 1.0)
+    if complex_:
+        im = uniform(seed, 2, (b + 1, n), -1.0, 1.0)
+        im[0, :] = 0.0
+        W = W + 1j * im
+    _clear_outside(W, n, b)
+    return W
+
+
+def band_dft(n: int, b: int, seed: int, complex_: bool = False, decay: float = 16.0) -> np.ndarray:
+    """DFT-like band: sorted U[-10,10] diagonal, N(0,1)*exp(-d/decay) off-diagonals."""
+    W = np.zeros((b + 1, n), dtype=np.complex128 if complex_ else np.float64)
+    W[0, :] = np.sort(uniform(seed, 1, (n,), -10.0, 10.0))
+    scale = np.exp(-np.arange(1, b + 1, dtype=np.float64) / decay)[:, None]
+    off = normal(seed, 2, (b, n)) * scale
+    if complex_:
+        off = off + 1j * (normal(seed, 3, (b, n)) * scale)
+    W[1:, :] = off
+    _clear_outside(W, n, b)
+    return W
+
+
+def _clear_outside(W: np.ndarray, n: int, b: int) -> None:
+    for d in range(1, b + 1):
+        W[d, max(0, n - d):] = 0.0
+
+
+def band_to_dense(W: np.ndarray) -> np.ndarray:
+    """Dense symmetric/Hermitian matrix from lower band storage (for checks)."""
+    b = W.shape[0] - 1
+    n = W.shape[1]
+    A = np.zeros((n, n), dtype=W.dtype)
+    for d in range(0, b + 1):
+        idx = np.arange(0, n - d)
+        A[idx + d, idx] = W[d, : n - d]
+        if d:
+            A[idx, idx + d] = np.conj(W[d, : n - d])
+    return A
+
+
+def toeplitz_band(n: int, b: int, a: float, offdiag: complex) -> np.ndarray:
+    """A tridiagonal Toeplitz matrix (diagonal ``a``, sub-diagonal ``offdiag``)
+    embedded in lower band storage of semi-bandwidth ``b`` (all other band
+    entries zero)."""
+    dt = np.complex128 if isinstance(offdiag, complex) else np.float64
+    W = np.zeros((b + 1, n), dtype=dt)
+    W[0, :] = a
+    if b >= 1:
+        W[1, : n - 1] = offdiag
+    return W
+
+
+# ----------------------------------------------------------------------------
+# eigenvector blocks and reflector stores (the inputs of Eq. 6d)
+# ----------------------------------------------------------------------------
+
+def eigvec_block(n: int, nev: int, seed: int, complex_: bool = False, ldq: int | None = None) -> np.ndarray:
+    """A dense n x nev block (column-major, leading dimension ``ldq``) with
+    N(0, 1/n) entries; returned as an (ldq, nev) Fortran-ordered array whose
+    rows n..ldq-1 are NaN so that a kernel touching them is caught."""
+    ldq = n if ldq is None else ldq
+    X = np.full((ldq, nev), np.nan, dtype=np.complex128 if complex_ else np.float64, order="F")
+    s = 1.0 / math.sqrt(max(n, 1))
+    body = normal(seed, 11, (nev, n)).T * s
+    if complex_:
+        body = body + 1j * (normal(seed, 12, (nev, n)).T * s)
+        body = body / math.sqrt(2.0)
+    X[:n, :] = body
+    return X
+
+
+def store_lengths(n: int, b: int, complex_: bool) -> np.ndarray:
+    """Lengths L_k of the reflectors in generation order (the canonical store
+    format: stage i = 0..n-3, sweep j = 0..ceil((n-i-2)/b)-1, L = min(b, n-r)
+    with r = i+1+j*b; a Hermitian store ends with one length-1 reflector)."""
+    out = []
+    for i in range(0, max(n - 2, 0)):
+        s = -(-(n - i - 2) // b)
+        for j in range(s):
+            r = i + 1 + j * b
+            out.append(min(b, n - r))
+    if complex_ and n >= 2:
+        out.append(1)
+    return np.asarray(out, dtype=np.int64)
+
+
+def synthetic_store(n: int, b: int, seed: int, complex_: bool = False):
+    """Random unitary Householder reflectors in the canonical store layout.
+
+    Returns ``(hh_v, hh_tau)``: ``hh_v`` is K x b column-major (reflector k is
+    the contiguous slice ``hh_v[k*b:(k+1)*b]``) with ``v[0] = 1`` stored and
+    zeros at positions >= L_k; ``hh_tau`` has K entries. Entries v[1:L] are
+    N(0, 1/L) draws; tau is chosen so that I - tau v v^H is unitary:
+    tau = 2/|v|^2 for real data and tau = (1 - exp(i*theta))/|v|^2 with
+    theta ~ U[0, 2pi) for complex data. Used where the stores of real
+    reductions are too slow to produce on the host; the back-transform's cost
+    does not depend on the values.
+    """
+    L = store_lengths(n, b, complex_)
+    K = len(L)
+    dt = np.complex128 if complex_ else np.float64
+    V = normal(seed, 21, (K, b)) / math.sqrt(max(b, 1))
+    if complex_:
+        V = V + 1j * (normal(seed, 22, (K, b)) / math.sqrt(max(b, 1)))
+    V = V.astype(dt)
+    cols = np.arange(b)[None, :]
+    V[cols >= L[:, None]] = 0.0
+    V[:, 0] = 1.0
+    nrm2 = np.sum(np.abs(V) ** 2, axis=1)
+    if complex_:
+        theta = uniform(seed, 23, (K,), 0.0, 2.0 * math.pi)
+        tau = (1.0 - np.exp(1j * theta)) / nrm2
+    else:
+        tau = 2.0 / nrm2
+    return np.ascontiguousarray(V.reshape(-1)), np.ascontiguousarray(tau.astype(dt))
+
+
+# ----------------------------------------------------------------------------
+# named workloads
+# ----------------------------------------------------------------------------
+
+WORKLOADS = {
+    # name: (n, b, nev, complex, band kind, seed)
+    "real-n512-b32-uniform": dict(n=512, b=32, nev=512, complex_=False, kind="uniform", seed=SEED_BASE + 1),
+    "real-n8192-b64-dft": dict(n=8192, b=64, nev=4096, complex_=False, kind="dft", seed=SEED_BASE + 2),
+    "complex-n20000-b64-dft": dict(n=20000, b=64, nev=6000, complex_=True, kind="dft", seed=SEED_BASE + 3),
+    "real-n32768-b64-dft": dict(n=32768, b=64, nev=9830, complex_=False, kind="dft", seed=SEED_BASE + 4),
+}
+
+
+def band_for(name: str, n: int | None = None) -> np.ndarray:
+    w = WORKLOADS[name]
+    n = w["n"] if n is None else n
+    f = band_uniform if w["kind"] == "uniform" else band_dft
+    return f(n, w["b"], w["seed"], w["complex_"])
+
+
+def batch_sizes(count: int = 64, seed: int = SEED_BASE + 5, lo: int = 1000, hi: int = 6000) -> np.ndarray:
+    """Problem sizes of the batched workload: N_p = lo + floor(u*(hi-lo+1))."""
+    u = uniform(seed, 31, (count,))
+    return (lo + np.floor(u * (hi - lo + 1))).astype(np.int64)
