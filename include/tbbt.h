@@ -1,0 +1,166 @@
+/*
+ * tbbt -- tridiagonal -> band eigenvector back-transformation on GB300.
+ *
+ * C ABI of the library libtbbt.so. It computes step Eq. 6d of the two-stage
+ * symmetric / Hermitian eigensolver of arXiv 2002.10991 (ELPA2),
+ *
+ *     Z = Q^* X = H_0 H_1 ... H_{K-1} X,      H_k = I - tau_k v_k v_k^H,
+ *
+ * i.e. every Householder reflector generated by the band -> tridiagonal
+ * bulge chase (Eq. 6b, Eq. 7, Sec. 2.2.1) applied to an n x nev block of
+ * eigenvectors in the reverse of generation order (Sec. 2.2.2), each one as
+ * x <- x - tau v (v^H x) (Eq. 8). Real symmetric problems use double,
+ * Hermitian problems complex double (two doubles, real part first, the
+ * layout of C99 double complex, cuDoubleComplex and numpy complex128).
+ *
+ * ---------------------------------------------------------------------------
+ * The reflector store (canonical input format)
+ * ---------------------------------------------------------------------------
+ * Reflectors are numbered k = 0..K-1 in generation order: stage i = 0..n-3,
+ * and within stage i the sweeps j = 0..ceil((n-i-2)/b)-1 (Sec. 2.2.1; the
+ * printed sweep count "(N-i)/b" is read as ceil((N-i-1)/b) with 1-based i,
+ * which reproduces the paper's N=17, b=4 example). A Hermitian store ends
+ * with one more reflector (stage n-2, sweep 0) of length 1 that makes the
+ * last sub-diagonal entry real. Reflector k acts on rows
+ *     r_k = i + 1 + j*b  ..  r_k + L_k - 1,    L_k = min(b, n - r_k)
+ * (0-based rows), so r_k and L_k follow from (n, b) and need no index array.
+ *
+ *   hh_v    K x b, column-major: reflector k is hh_v[k*b .. k*b + b); its
+ *           first entry v_k[0] = 1 is stored explicitly; entries at
+ *           positions >= L_k are ignored (conventionally zero).
+ *   hh_tau  K scalars tau_k (complex for Hermitian problems, LAPACK
+ *           convention: H_k^H x = beta e_1 with real beta in the reduction).
+ *
+ * tbbt_num_reflectors(n, b, is_complex) returns K.
+ *
+ * ---------------------------------------------------------------------------
+ * Conventions of every call
+ * ---------------------------------------------------------------------------
+ * - Pointers named d_* or documented as device pointers are device memory
+ *   owned by the caller; the library never frees them.
+ * - q is n x nev, column-major, leading dimension ldq >= max(1, n), and is
+ *   overwritten with Z. Rows n..ldq-1 are never read or written.
+ * - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *   stream) with no host synchronisation, except where a call says it
+ *   allocates. Errors found on the host are returned at once; faults of
+ *   enqueued work surface in later CUDA calls; bounded waits inside kernels
+ *   that give up record TBBT_ETIMEOUT in a device word that
+ *   tbbt_stream_check() reports.
+ * - No exception crosses the ABI. NaN or Inf in the inputs propagates to the
+ *   affected columns; it is not checked.
+ * - Device: compute capability 10.3 (GB300, sm_103a).
+ */
+#ifndef TBBT_H
+#define TBBT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TBBT_OK = 0,
+  TBBT_EINVAL = 1,   /* invalid argument (size, pointer, alignment, leading dimension) */
+  TBBT_ENOMEM = 2,   /* device or host allocation failed */
+  TBBT_ECUDA = 3,    /* a CUDA runtime call failed */
+  TBBT_ETIMEOUT = 4, /* a bounded in-kernel wait gave up (reported by tbbt_stream_check) */
+  TBBT_ENOTSUP = 5   /* valid request this build does not support (e.g. variant / size) */
+} tbbt_status;
+
+typedef enum { TBBT_REAL64 = 0, TBBT_COMPLEX128 = 1 } tbbt_dtype;
+
+/* Human-readable name of a status code (static string). */
+const char *tbbt_status_string(tbbt_status s);
+
+/* Number of reflectors K in the store of an n x n problem with semi-bandwidth
+ * b (Sec. 2.2.1: N-2 stages, ceil((N-i-1)/b) sweeps in 1-based stage i; one
+ * more for Hermitian problems). Returns -1 for n < 0 or b < 1. */
+int64_t tbbt_num_reflectors(int64_t n, int64_t b, int is_complex);
+
+/* ---------------------------------------------------------------------------
+ * One-shot calls (Eq. 6d). hh_v, hh_tau and q are device pointers.
+ *
+ * n >= 0, 1 <= nbw <= 128, 0 <= nev <= n, ldq >= max(1, n); q aligned to its
+ * element size. The first call for a given (dtype, n, nbw, nev) allocates a
+ * cached workspace (a host-synchronising cudaMalloc); later calls with the
+ * same shape reuse it and do not synchronise. Calls sharing a shape must not
+ * overlap on different streams (they share the workspace); use plans for
+ * that. The cache lives until tbbt_release_cache() or process exit.
+ * ------------------------------------------------------------------------- */
+tbbt_status tbbt_trans_ev_tridi_to_band_d(const double *hh_v, const double *hh_tau, int64_t n, int64_t nbw,
+                                          int64_t nev, double *q, int64_t ldq, void *stream);
+/* Complex double: each pointer addresses interleaved (re, im) pairs. */
+tbbt_status tbbt_trans_ev_tridi_to_band_z(const void *hh_v, const void *hh_tau, int64_t n, int64_t nbw,
+                                          int64_t nev, void *q, int64_t ldq, void *stream);
+
+/* Same computation with every array in HOST memory (pinned memory makes the
+ * copies asynchronous). The call copies the store and X to the device, runs
+ * the back-transform and copies Z back into q, all on `stream`; the caller
+ * synchronises the stream before reading q. Uses the one-shot cache plus a
+ * cached device copy of the inputs. */
+tbbt_status tbbt_trans_ev_tridi_to_band_host_d(const double *hh_v, const double *hh_tau, int64_t n,
+                                               int64_t nbw, int64_t nev, double *q, int64_t ldq, void *stream);
+tbbt_status tbbt_trans_ev_tridi_to_band_host_z(const void *hh_v, const void *hh_tau, int64_t n, int64_t nbw,
+                                               int64_t nev, void *q, int64_t ldq, void *stream);
+
+/* Frees every workspace cached by the one-shot calls (synchronises the device). */
+tbbt_status tbbt_release_cache(void);
+
+/* ---------------------------------------------------------------------------
+ * Plans: all device allocation happens in tbbt_plan_create (the paper's
+ * advice to pre-compute and pre-allocate workspace outside the work loop,
+ * Sec. 3.1); set_reflectors and execute only enqueue kernels.
+ * ------------------------------------------------------------------------- */
+typedef struct tbbt_plan tbbt_plan;
+
+typedef struct {
+  /* Sweeps processed concurrently by one thread block (one warp each);
+   * 0 = choose automatically. */
+  int32_t sweeps_per_block;
+  /* Stages each warp applies between two block-wide synchronisations;
+   * 0 = choose automatically. */
+  int32_t stages_per_step;
+  int32_t reserved[6];
+} tbbt_options;
+
+/* Creates a plan for problems of the given type and shape (arguments as for
+ * the one-shot calls). opt may be NULL. Allocates the re-laid reflector
+ * store (K * round_up(nbw, 2) elements) and small tables; synchronises. */
+tbbt_status tbbt_plan_create(tbbt_plan **plan, tbbt_dtype dtype, int64_t n, int64_t nbw, int64_t nev,
+                             const tbbt_options *opt);
+
+/* Re-lays the canonical store (device pointers hh_v, hh_tau in the format
+ * above) into the plan's sweep-major layout (Sec. 3.2: one process applies
+ * consecutive reflectors of a sweep, each shifted up by one row). Enqueued on
+ * `stream`; the input arrays may be reused once the stream reaches this point. */
+tbbt_status tbbt_plan_set_reflectors(tbbt_plan *plan, const void *hh_v, const void *hh_tau, void *stream);
+
+/* Applies the reflectors set last to q (device pointer, n x nev, ldq) in place. */
+tbbt_status tbbt_plan_execute(tbbt_plan *plan, void *q, int64_t ldq, void *stream);
+
+/* Destroys a plan (synchronises the device). Accepts NULL. */
+tbbt_status tbbt_plan_destroy(tbbt_plan *plan);
+
+/* Launch geometry a plan chose (for the benchmark and tests): sweeps per
+ * block, stages per step, ring rows, dynamic shared memory bytes, blocks. */
+tbbt_status tbbt_plan_info(const tbbt_plan *plan, int32_t *sweeps_per_block, int32_t *stages_per_step,
+                           int32_t *ring_rows, int32_t *smem_bytes, int32_t *blocks);
+
+/* Synchronises `stream`, then reports (and clears) the device error word:
+ * TBBT_OK, TBBT_ETIMEOUT, or TBBT_ECUDA if the stream itself failed. */
+tbbt_status tbbt_stream_check(void *stream);
+
+/* Host-side check of the block schedule (no GPU needed): largest number of
+ * rows a thread block ever holds at once for these parameters, or -1 if the
+ * schedule would touch a row twice in one step. Used by tests to show the
+ * shared-memory ring never wraps onto live rows. */
+int64_t tbbt_schedule_max_live_rows(int64_t n, int64_t nbw, int is_complex, int32_t sweeps_per_block,
+                                    int32_t stages_per_step);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TBBT_H */

@@ -1,0 +1,14 @@
+"""GB300-native tridiagonal -> band eigenvector back-transformation
+(arXiv 2002.10991, Eq. 6d): a CUDA library behind a C ABI (include/tbbt.h)
+and this thin Python binding."""
+
+from .api import (  # noqa: F401
+    Plan,
+    TbbtError,
+    num_reflectors,
+    release_cache,
+    schedule_max_live_rows,
+    stream_check,
+    trans_ev_tridi_to_band,
+    trans_ev_tridi_to_band_host,
+)

@@ -1,0 +1,173 @@
+"""Python binding of libtbbt (names follow the C ABI in include/tbbt.h).
+
+Argument marshalling only: tensors are passed as raw pointers and the
+caller's current CUDA stream; every step of the computation runs in the
+library's kernels. PyTorch provides device memory and streams.
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _native
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTSUP = range(6)
+REAL64, COMPLEX128 = 0, 1
+
+
+class TbbtError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _native.load().tbbt_status_string(status).decode()
+        super().__init__(f"{where}: {msg} (status {status})")
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        raise TbbtError(status, where)
+
+
+def _stream_handle(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+def _is_complex_dtype(t) -> bool:
+    import torch
+
+    if t.dtype == torch.complex128:
+        return True
+    if t.dtype == torch.float64:
+        return False
+    raise TypeError(f"expected float64 or complex128, got {t.dtype}")
+
+
+def num_reflectors(n: int, nbw: int, is_complex: bool) -> int:
+    return int(_native.load().tbbt_num_reflectors(n, nbw, int(is_complex)))
+
+
+def schedule_max_live_rows(n: int, nbw: int, is_complex: bool, sweeps_per_block: int, stages_per_step: int) -> int:
+    return int(_native.load().tbbt_schedule_max_live_rows(n, nbw, int(is_complex), sweeps_per_block, stages_per_step))
+
+
+def _q_layout(q, n):
+    """(ldq, nev) of a column-major (Fortran-ordered) 2-D tensor view."""
+    if q.dim() != 2:
+        raise ValueError("q must be 2-D (ldq >= n rows, nev columns), column-major")
+    rows, nev = q.shape
+    if nev > 1 and q.stride(0) != 1:
+        raise ValueError("q must be column-major (stride(0) == 1)")
+    ldq = q.stride(1) if nev > 1 else max(rows, 1)
+    if rows < n:
+        raise ValueError("q has fewer than n rows")
+    return ldq, nev
+
+
+def trans_ev_tridi_to_band(hh_v, hh_tau, n: int, nbw: int, nev: int, q, ldq: int | None = None, stream=None):
+    """Eq. 6d on device tensors: q[:n, :nev] <- H_0 ... H_{K-1} q[:n, :nev].
+
+    hh_v (K*nbw,), hh_tau (K,), q (ldq x >=nev, column-major) are CUDA
+    tensors of dtype float64 (real symmetric) or complex128 (Hermitian)."""
+    cplx = _is_complex_dtype(q)
+    if ldq is None:
+        ldq, _ = _q_layout(q, n)
+    L = _native.load()
+    f = L.tbbt_trans_ev_tridi_to_band_z if cplx else L.tbbt_trans_ev_tridi_to_band_d
+    st = f(ctypes.c_void_p(hh_v.data_ptr() if hh_v.numel() else 0),
+           ctypes.c_void_p(hh_tau.data_ptr() if hh_tau.numel() else 0),
+           n, nbw, nev, ctypes.c_void_p(q.data_ptr() if q.numel() else 0), ldq, _stream_handle(stream))
+    _check(st, "tbbt_trans_ev_tridi_to_band")
+    return q
+
+
+def trans_ev_tridi_to_band_host(hh_v, hh_tau, n: int, nbw: int, nev: int, q, ldq: int | None = None, stream=None,
+                                synchronize: bool = True):
+    """The same with every array in host memory (numpy arrays or CPU
+    tensors; pinned memory makes the copies asynchronous). q is updated in
+    place; with ``synchronize`` the call waits for the stream."""
+    def ptr(a):
+        if isinstance(a, np.ndarray):
+            return a.ctypes.data if a.size else 0
+        return a.data_ptr() if a.numel() else 0
+
+    if isinstance(q, np.ndarray):
+        cplx = np.iscomplexobj(q)
+        if ldq is None:
+            ldq = q.shape[0]
+        if not q.flags.f_contiguous:
+            raise ValueError("q must be Fortran-ordered")
+    else:
+        cplx = _is_complex_dtype(q)
+        if ldq is None:
+            ldq, _ = _q_layout(q, n)
+    L = _native.load()
+    f = L.tbbt_trans_ev_tridi_to_band_host_z if cplx else L.tbbt_trans_ev_tridi_to_band_host_d
+    h = _stream_handle(stream)
+    st = f(ctypes.c_void_p(ptr(hh_v)), ctypes.c_void_p(ptr(hh_tau)), n, nbw, nev, ctypes.c_void_p(ptr(q)), ldq, h)
+    _check(st, "tbbt_trans_ev_tridi_to_band_host")
+    if synchronize:
+        _check(L.tbbt_stream_check(h), "tbbt_stream_check")
+    return q
+
+
+def release_cache():
+    _check(_native.load().tbbt_release_cache(), "tbbt_release_cache")
+
+
+def stream_check(stream=None):
+    """Synchronise the stream and raise TbbtError if an in-kernel wait gave up."""
+    _check(_native.load().tbbt_stream_check(_stream_handle(stream)), "tbbt_stream_check")
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("sweeps_per_block", ctypes.c_int32), ("stages_per_step", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
+class Plan:
+    """tbbt_plan: workspace allocated once, then set_reflectors / execute."""
+
+    def __init__(self, dtype_complex: bool, n: int, nbw: int, nev: int, sweeps_per_block: int = 0,
+                 stages_per_step: int = 0):
+        self.n, self.nbw, self.nev, self.complex = n, nbw, nev, dtype_complex
+        self._h = ctypes.c_void_p()
+        opt = Options(sweeps_per_block, stages_per_step)
+        st = _native.load().tbbt_plan_create(ctypes.byref(self._h), COMPLEX128 if dtype_complex else REAL64,
+                                             n, nbw, nev, ctypes.byref(opt))
+        _check(st, "tbbt_plan_create")
+
+    def set_reflectors(self, hh_v, hh_tau, stream=None):
+        st = _native.load().tbbt_plan_set_reflectors(
+            self._h, ctypes.c_void_p(hh_v.data_ptr() if hh_v.numel() else 0),
+            ctypes.c_void_p(hh_tau.data_ptr() if hh_tau.numel() else 0), _stream_handle(stream))
+        _check(st, "tbbt_plan_set_reflectors")
+
+    def execute(self, q, ldq: int | None = None, stream=None):
+        if ldq is None:
+            ldq, _ = _q_layout(q, self.n)
+        st = _native.load().tbbt_plan_execute(self._h, ctypes.c_void_p(q.data_ptr() if q.numel() else 0), ldq,
+                                              _stream_handle(stream))
+        _check(st, "tbbt_plan_execute")
+        return q
+
+    def info(self):
+        vals = [ctypes.c_int32() for _ in range(5)]
+        _check(_native.load().tbbt_plan_info(self._h, *[ctypes.byref(v) for v in vals]), "tbbt_plan_info")
+        keys = ("sweeps_per_block", "stages_per_step", "ring_rows", "smem_bytes", "blocks")
+        return dict(zip(keys, (v.value for v in vals)))
+
+    def close(self):
+        if self._h:
+            _native.load().tbbt_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,289 @@
+// Kernels of the tridiagonal -> band back-transformation (Eq. 6d).
+//
+//   relayout_kernel  canonical store -> sweep-major store (tau folded in)
+//   apply_kernel     applies every reflector to the columns of q (Eq. 8)
+//
+// Design (GB300): FP64 runs at 2 DFMA/clock/SM, one warp instruction per 64
+// clocks per sub-partition, and a single warp with a dependent FMA chain
+// already saturates it. So the kernel spends its FP64 issue slots on the
+// 2L FMAs per column that Eq. 8 needs and on nothing else: one lane owns one
+// column (dot product and update are serial per lane; no cross-lane
+// reductions, which would cost extra FP64 adds), and parallelism beyond the
+// columns comes from running several sweeps of a strip at once (see
+// schedule.cuh). Rows of the 32-column strip live in a shared-memory ring
+// indexed [row % ring][lane] (conflict-free 8/16-byte lane accesses); rows
+// stream in through cp.async and are written back once the last sweep of
+// the epoch has passed them. Reflectors stream per warp into double-buffered
+// shared memory.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "schedule.cuh"
+
+namespace tbbt {
+
+struct alignas(16) zdouble {
+  double re, im;
+};
+
+// ---------------------------------------------------------------------------
+// arithmetic of one element type
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Arith;
+
+template <>
+struct Arith<double> {
+  // s += conj(v) * x
+  static __device__ __forceinline__ void dot(double &s, double v, double x) { s = fma(v, x, s); }
+  // u = tau * s
+  static __device__ __forceinline__ double scale(double tau, double s) { return tau * s; }
+  // x -= u * v
+  static __device__ __forceinline__ void axpy(double &x, double u, double v) { x = fma(-u, v, x); }
+  static __device__ __forceinline__ void sub(double &x, double u) { x -= u; }
+  static __device__ __forceinline__ double zero() { return 0.0; }
+};
+
+template <>
+struct Arith<zdouble> {
+  static __device__ __forceinline__ void dot(zdouble &s, zdouble v, zdouble x) {
+    s.re = fma(v.re, x.re, s.re);
+    s.re = fma(v.im, x.im, s.re);
+    s.im = fma(v.re, x.im, s.im);
+    s.im = fma(-v.im, x.re, s.im);
+  }
+  static __device__ __forceinline__ zdouble scale(zdouble t, zdouble s) {
+    zdouble u;
+    u.re = fma(t.re, s.re, -t.im * s.im);
+    u.im = fma(t.re, s.im, t.im * s.re);
+    return u;
+  }
+  static __device__ __forceinline__ void axpy(zdouble &x, zdouble u, zdouble v) {
+    x.re = fma(-u.re, v.re, x.re);
+    x.re = fma(u.im, v.im, x.re);
+    x.im = fma(-u.re, v.im, x.im);
+    x.im = fma(-u.im, v.re, x.im);
+  }
+  static __device__ __forceinline__ void sub(zdouble &x, zdouble u) {
+    x.re -= u.re;
+    x.im -= u.im;
+  }
+  static __device__ __forceinline__ zdouble zero() { return zdouble{0.0, 0.0}; }
+};
+
+// ---------------------------------------------------------------------------
+// store re-layout
+// ---------------------------------------------------------------------------
+// The canonical store numbers reflectors in generation order (stage-major).
+// The apply kernel reads them sweep-major: sweep j, stages imax(j) .. 0, so a
+// warp streams consecutive reflectors of its sweep from one contiguous
+// range. Entry layout (ldv = b rounded up to even, 16-byte aligned):
+//   [tau, v1, v2, ..., v_{L-1}, 0, ...]      (v0 = 1 is implicit)
+// stage_off[s] = generation index of reflector (s, 0).
+template <typename T>
+__global__ void relayout_kernel(const T *__restrict__ hh_v, const T *__restrict__ hh_tau,
+                                const int64_t *__restrict__ stage_off, StoreGeom g, int32_t ldv,
+                                T *__restrict__ out) {
+  const int64_t K = g.num_reflectors();
+  const int32_t J = g.num_sweeps();
+  // one warp per destination entry
+  int64_t entry = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  if (entry >= K) return;
+  // find sweep j with sweep_offset(j) <= entry < sweep_offset(j+1)
+  int32_t lo = 0, hi = J - 1;
+  while (lo < hi) {
+    int32_t mid = (lo + hi + 1) >> 1;
+    if (g.sweep_offset(mid) <= entry)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  int32_t j = lo;
+  int32_t s = g.imax(j) - (int32_t)(entry - g.sweep_offset(j));
+  int64_t k = stage_off[s] + j;
+  int32_t L = g.len(s, j);
+  const T *src = hh_v + k * g.b;
+  T *dst = out + entry * ldv;
+  for (int32_t t = lane; t < ldv; t += 32) {
+    T val = Arith<T>::zero();
+    if (t == 0)
+      val = hh_tau[k];
+    else if (t < L)
+      val = src[t];
+    dst[t] = val;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// async-copy helpers (sm_80+ cp.async; completion by wait_all + barrier)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *dst_smem, const void *src_gmem) {
+  if constexpr (BYTES == 16) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst_smem)), "l"(src_gmem));
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst_smem)), "l"(src_gmem));
+  }
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
+// the apply kernel
+// ---------------------------------------------------------------------------
+struct ApplyArgs {
+  const void *vstore;  // sweep-major store, ldv elements per reflector
+  void *q;
+  int64_t ldq;
+  StoreGeom g;
+  int32_t nev;
+  int32_t ldv;
+  int32_t G;     // sweeps (warps) per block
+  int32_t NB;    // stages per step
+  int32_t ring;  // rows in the shared-memory ring
+  int *err;
+};
+
+// Rows [r0, r1) of the strip: global -> ring (cp.async). Columns >= nev are
+// zero-filled so that idle lanes compute on zeros.
+template <typename T>
+__device__ __forceinline__ void load_rows(const ApplyArgs &a, T *ring, int32_t r0, int32_t r1, int32_t c0) {
+  const int32_t nrows = r1 - r0;
+  if (nrows <= 0) return;
+  const T *q = reinterpret_cast<const T *>(a.q);
+  const int32_t total = nrows * 32;
+  for (int32_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    int32_t c = idx / nrows;
+    int32_t r = r0 + (idx - c * nrows);
+    T *dst = ring + (int64_t)(r % a.ring) * 32 + c;
+    int32_t col = c0 + c;
+    if (col < a.nev) {
+      cp_async<sizeof(T)>(dst, q + (int64_t)col * a.ldq + r);
+    } else {
+      *dst = Arith<T>::zero();
+    }
+  }
+}
+
+// Rows [r0, r1): ring -> global.
+template <typename T>
+__device__ __forceinline__ void store_rows(const ApplyArgs &a, const T *ring, int32_t r0, int32_t r1, int32_t c0) {
+  const int32_t nrows = r1 - r0;
+  if (nrows <= 0) return;
+  T *q = reinterpret_cast<T *>(a.q);
+  const int32_t total = nrows * 32;
+  for (int32_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    int32_t c = idx / nrows;
+    int32_t r = r0 + (idx - c * nrows);
+    int32_t col = c0 + c;
+    if (col < a.nev) q[(int64_t)col * a.ldq + r] = ring[(int64_t)(r % a.ring) * 32 + c];
+  }
+}
+
+// Reflector entries of warp w for its block at step t -> its buffer slot.
+template <typename T>
+__device__ __forceinline__ void load_reflectors(const ApplyArgs &a, const Epoch &ep, T *vbuf_w, int32_t w,
+                                                int32_t t, int lane) {
+  int32_t hi, lo;
+  warp_stages(a.g, ep, w, t, &hi, &lo);
+  if (hi < lo) return;
+  const int32_t j = ep.j0 + w;
+  const int32_t sig = ep.sig_top - (t - w) * ep.nb;
+  const T *src = reinterpret_cast<const T *>(a.vstore) + (a.g.sweep_offset(j) + (a.g.imax(j) - hi)) * a.ldv;
+  T *dst = vbuf_w + (int64_t)(t & 1) * ep.nb * a.ldv + (int64_t)(sig - hi) * a.ldv;
+  // (hi - lo + 1) * ldv elements, contiguous on both sides, 16-byte chunks
+  const int32_t nchunks = (hi - lo + 1) * a.ldv * (int32_t)sizeof(T) / 16;
+  const char *s8 = reinterpret_cast<const char *>(src);
+  char *d8 = reinterpret_cast<char *>(dst);
+  for (int32_t c = lane; c < nchunks; c += 32) cp_async<16>(d8 + 16 * c, s8 + 16 * c);
+}
+
+// Eq. 8 for one reflector on one column: x[r:r+L] -= tau * v * (v^H x[r:r+L]).
+template <typename T>
+__device__ __forceinline__ void apply_one(T *col, int32_t ring, int32_t r, int32_t L, const T *ent) {
+  int32_t base = r % ring;
+  T s = col[(int64_t)base * 32];
+  {
+    int32_t sl = base;
+#pragma unroll 4
+    for (int32_t t = 1; t < L; ++t) {
+      sl = (sl + 1 == ring) ? 0 : sl + 1;
+      Arith<T>::dot(s, ent[t], col[(int64_t)sl * 32]);
+    }
+  }
+  const T u = Arith<T>::scale(ent[0], s);
+  {
+    T x0 = col[(int64_t)base * 32];
+    Arith<T>::sub(x0, u);
+    col[(int64_t)base * 32] = x0;
+    int32_t sl = base;
+#pragma unroll 4
+    for (int32_t t = 1; t < L; ++t) {
+      sl = (sl + 1 == ring) ? 0 : sl + 1;
+      T x = col[(int64_t)sl * 32];
+      Arith<T>::axpy(x, u, ent[t]);
+      col[(int64_t)sl * 32] = x;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512, 1) apply_kernel(ApplyArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *ring = reinterpret_cast<T *>(smem_raw);
+  T *vbuf = ring + (int64_t)a.ring * 32;
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  const int32_t c0 = blockIdx.x * 32;
+  const StoreGeom &g = a.g;
+  const int32_t J = g.num_sweeps();
+  T *vbuf_w = vbuf + (int64_t)w * 2 * a.NB * a.ldv;
+  T *mycol = ring + lane;
+
+  for (int32_t e = 0; e * a.G < J; ++e) {
+    const Epoch ep = make_epoch(g, e, a.G, a.NB);
+    // prologue: rows needed at step 0 and the reflectors of step 0
+    int32_t top = step_min_row(g, ep, 0);
+    load_rows<T>(a, ring, top, g.n, c0);
+    load_reflectors<T>(a, ep, vbuf_w, w, 0, lane);
+    cp_async_wait_all();
+    __syncthreads();
+    int32_t released = g.n;  // rows >= released are back in global memory
+    for (int32_t t = 0; t < ep.nsteps; ++t) {
+      // rows no warp touches from step t on
+      int32_t live = rows_live_max(g, ep, t);
+      int32_t rel = live + 1 > top ? live + 1 : top;
+      if (rel < released) {
+        store_rows<T>(a, ring, rel, released, c0);
+        released = rel;
+      }
+      // prefetch rows and reflectors of step t+1
+      int32_t ntop = step_min_row(g, ep, t + 1);
+      load_rows<T>(a, ring, ntop, top, c0);
+      top = ntop;
+      load_reflectors<T>(a, ep, vbuf_w, w, t + 1, lane);
+      // apply this warp's stages of step t
+      int32_t hi, lo;
+      warp_stages(g, ep, w, t, &hi, &lo);
+      if (hi >= lo) {
+        const int32_t j = ep.j0 + w;
+        const int32_t sig = ep.sig_top - (t - w) * ep.nb;
+        const T *vb = vbuf_w + (int64_t)(t & 1) * ep.nb * a.ldv;
+        for (int32_t s = hi; s >= lo; --s) {
+          apply_one<T>(mycol, a.ring, g.row(s, j), g.len(s, j), vb + (int64_t)(sig - s) * a.ldv);
+        }
+      }
+      cp_async_wait_all();
+      __syncthreads();
+    }
+    // flush the rows still resident
+    store_rows<T>(a, ring, top, released, c0);
+    __syncthreads();
+  }
+}
+
+}  // namespace tbbt

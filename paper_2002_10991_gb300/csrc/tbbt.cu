@@ -1,0 +1,410 @@
+// Host side of libtbbt: argument checking, plans, the one-shot cache and the
+// C ABI declared in include/tbbt.h. Every step of the computation runs in the
+// kernels of apply_kernels.cuh; this file only validates, allocates and
+// launches.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "../../include/tbbt.h"
+#include "apply_kernels.cuh"
+
+using tbbt::StoreGeom;
+using tbbt::zdouble;
+
+namespace {
+
+constexpr int32_t kMaxBand = 128;
+constexpr int32_t kMaxSmem = 227 * 1024;
+
+#define TBBT_CUDA_TRY(expr)                          \
+  do {                                               \
+    cudaError_t e_ = (expr);                         \
+    if (e_ != cudaSuccess) {                         \
+      (void)cudaGetLastError();                      \
+      return e_ == cudaErrorMemoryAllocation ? TBBT_ENOMEM : TBBT_ECUDA; \
+    }                                                \
+  } while (0)
+
+// Device error word set by bounded in-kernel waits that gave up.
+__device__ int g_tbbt_error = 0;
+
+int32_t round_even(int32_t b) { return (b + 1) & ~1; }
+
+size_t elem_size(tbbt_dtype dt) { return dt == TBBT_COMPLEX128 ? 16 : 8; }
+
+int32_t ring_rows_for(int32_t b, int32_t G, int32_t NB) { return G * b + (G + 2) * NB + 8; }
+
+size_t smem_bytes_for(tbbt_dtype dt, int32_t b, int32_t G, int32_t NB) {
+  size_t es = elem_size(dt);
+  return (size_t)ring_rows_for(b, G, NB) * 32 * es + (size_t)G * 2 * NB * round_even(b) * es;
+}
+
+tbbt_status check_shape(int64_t n, int64_t nbw, int64_t nev) {
+  if (n < 0 || n > (int64_t)1 << 30) return TBBT_EINVAL;
+  if (nbw < 1 || nbw > kMaxBand) return TBBT_EINVAL;
+  if (nev < 0 || nev > n) return TBBT_EINVAL;
+  return TBBT_OK;
+}
+
+}  // namespace
+
+struct tbbt_plan {
+  tbbt_dtype dtype;
+  StoreGeom g;
+  int32_t nev;
+  int64_t K;
+  int32_t ldv;
+  int32_t G, NB, ring;
+  size_t smem;
+  void *d_store = nullptr;       // re-laid reflectors, K * ldv elements
+  int64_t *d_stage_off = nullptr;  // n entries
+  int *d_err = nullptr;
+  // device copies used by the host-buffer entry points (allocated on demand)
+  void *d_hv = nullptr, *d_ht = nullptr, *d_q = nullptr;
+  int64_t d_q_ld = 0;
+};
+
+extern "C" {
+
+const char *tbbt_status_string(tbbt_status s) {
+  switch (s) {
+    case TBBT_OK: return "ok";
+    case TBBT_EINVAL: return "invalid argument";
+    case TBBT_ENOMEM: return "out of memory";
+    case TBBT_ECUDA: return "CUDA error";
+    case TBBT_ETIMEOUT: return "in-kernel wait timed out";
+    case TBBT_ENOTSUP: return "not supported";
+  }
+  return "unknown status";
+}
+
+int64_t tbbt_num_reflectors(int64_t n, int64_t b, int is_complex) {
+  if (n < 0 || b < 1 || n > (int64_t)1 << 30 || b > (int64_t)1 << 30) return -1;
+  StoreGeom g{(int32_t)n, (int32_t)b, is_complex ? 1 : 0};
+  return g.num_reflectors();
+}
+
+int64_t tbbt_schedule_max_live_rows(int64_t n, int64_t nbw, int is_complex, int32_t G, int32_t NB) {
+  if (n < 0 || nbw < 1 || G < 1 || NB < 1 || n > (int64_t)1 << 24) return -1;
+  StoreGeom g{(int32_t)n, (int32_t)nbw, is_complex ? 1 : 0};
+  const int32_t J = g.num_sweeps();
+  int64_t worst = 0;
+  std::vector<int32_t> done_stage;  // lowest stage applied so far per sweep
+  std::vector<int64_t> count(J > 0 ? J : 1, 0);
+  for (int32_t e = 0; e * G < J; ++e) {
+    tbbt::Epoch ep = tbbt::make_epoch(g, e, G, NB);
+    done_stage.assign(ep.ge, INT32_MAX);
+    int32_t prev_live = g.n - 1;
+    for (int32_t t = 0; t < ep.nsteps; ++t) {
+      int32_t live = tbbt::rows_live_max(g, ep, t);
+      int32_t top = tbbt::step_min_row(g, ep, t);
+      int32_t ntop = tbbt::step_min_row(g, ep, t + 1);
+      // ring must hold [ntop, prev_live] without aliasing
+      int64_t need = (int64_t)prev_live - ntop + 1;
+      if (need > worst) worst = need;
+      int32_t last_max = -1;  // last row of the nearest active warp above
+      for (int32_t w = 0; w < ep.ge; ++w) {
+        int32_t hi, lo;
+        tbbt::warp_stages(g, ep, w, t, &hi, &lo);
+        if (hi < lo) continue;
+        int32_t j = ep.j0 + w;
+        int32_t rlo = g.row(lo, j);
+        int32_t rhi = g.row(hi, j) + g.len(hi, j) - 1;
+        if (rlo < top || rhi > live) return -1;  // outside the resident rows
+        if (rlo <= last_max) return -1;  // overlaps the warp above
+        last_max = rhi;
+        for (int32_t s = hi; s >= lo; --s) {
+          // sweep j-1 must have applied stage s+1 in an earlier step
+          if (w > 0 && done_stage[w - 1] > s + 1) return -1;
+          if (s > g.imax(j) || s < 0) return -1;
+          count[j] += 1;
+        }
+      }
+      for (int32_t w = 0; w < ep.ge; ++w) {
+        int32_t hi, lo;
+        tbbt::warp_stages(g, ep, w, t, &hi, &lo);
+        if (hi >= lo) done_stage[w] = lo;
+      }
+      prev_live = live;
+    }
+    for (int32_t w = 0; w < ep.ge; ++w)
+      if (done_stage[w] != 0) return -1;
+  }
+  for (int32_t j = 0; j < J; ++j)
+    if (count[j] != (int64_t)g.imax(j) + 1) return -1;
+  return worst;
+}
+
+tbbt_status tbbt_plan_create(tbbt_plan **plan, tbbt_dtype dtype, int64_t n, int64_t nbw, int64_t nev,
+                             const tbbt_options *opt) {
+  if (!plan) return TBBT_EINVAL;
+  *plan = nullptr;
+  if (dtype != TBBT_REAL64 && dtype != TBBT_COMPLEX128) return TBBT_EINVAL;
+  tbbt_status st = check_shape(n, nbw, nev);
+  if (st != TBBT_OK) return st;
+  tbbt_plan *p = new (std::nothrow) tbbt_plan();
+  if (!p) return TBBT_ENOMEM;
+  p->dtype = dtype;
+  p->g = StoreGeom{(int32_t)n, (int32_t)nbw, dtype == TBBT_COMPLEX128 ? 1 : 0};
+  p->nev = (int32_t)nev;
+  p->K = p->g.num_reflectors();
+  p->ldv = round_even((int32_t)nbw);
+  // launch geometry: most sweeps per block that fit in shared memory
+  int32_t wantG = opt && opt->sweeps_per_block > 0 ? opt->sweeps_per_block : 8;
+  int32_t wantNB = opt && opt->stages_per_step > 0 ? opt->stages_per_step : 8;
+  if (wantG > 16) wantG = 16;
+  int32_t G = wantG, NB = wantNB;
+  while (smem_bytes_for(dtype, (int32_t)nbw, G, NB) > (size_t)kMaxSmem) {
+    if (G > 4 || (NB <= 2 && G > 1))
+      --G;
+    else if (NB > 2)
+      NB /= 2;
+    else
+      break;
+  }
+  if (smem_bytes_for(dtype, (int32_t)nbw, G, NB) > (size_t)kMaxSmem) {
+    delete p;
+    return TBBT_ENOTSUP;
+  }
+  p->G = G;
+  p->NB = NB;
+  p->ring = ring_rows_for((int32_t)nbw, G, NB);
+  p->smem = smem_bytes_for(dtype, (int32_t)nbw, G, NB);
+
+  auto fail = [&](tbbt_status s) {
+    tbbt_plan_destroy(p);
+    return s;
+  };
+  cudaError_t e;
+  if (p->K > 0) {
+    e = cudaMalloc(&p->d_store, (size_t)p->K * p->ldv * elem_size(dtype));
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      return fail(TBBT_ENOMEM);
+    }
+    std::vector<int64_t> off((size_t)n + 1, 0);
+    int64_t k = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      off[(size_t)i] = k;
+      int64_t ns = (i + 3 <= n) ? (n - i - 2 + nbw - 1) / nbw : ((dtype == TBBT_COMPLEX128 && i == n - 2) ? 1 : 0);
+      k += ns;
+    }
+    e = cudaMalloc(&p->d_stage_off, sizeof(int64_t) * ((size_t)n + 1));
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      return fail(TBBT_ENOMEM);
+    }
+    e = cudaMemcpy(p->d_stage_off, off.data(), sizeof(int64_t) * ((size_t)n + 1), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(TBBT_ECUDA);
+  }
+  e = cudaGetSymbolAddress((void **)&p->d_err, g_tbbt_error);
+  if (e != cudaSuccess) return fail(TBBT_ECUDA);
+  if (dtype == TBBT_COMPLEX128)
+    e = cudaFuncSetAttribute(tbbt::apply_kernel<zdouble>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
+  else
+    e = cudaFuncSetAttribute(tbbt::apply_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
+  if (e != cudaSuccess) return fail(TBBT_ECUDA);
+  *plan = p;
+  return TBBT_OK;
+}
+
+tbbt_status tbbt_plan_info(const tbbt_plan *p, int32_t *G, int32_t *NB, int32_t *ring, int32_t *smem,
+                           int32_t *blocks) {
+  if (!p) return TBBT_EINVAL;
+  if (G) *G = p->G;
+  if (NB) *NB = p->NB;
+  if (ring) *ring = p->ring;
+  if (smem) *smem = (int32_t)p->smem;
+  if (blocks) *blocks = (p->nev + 31) / 32;
+  return TBBT_OK;
+}
+
+tbbt_status tbbt_plan_set_reflectors(tbbt_plan *p, const void *hh_v, const void *hh_tau, void *stream) {
+  if (!p) return TBBT_EINVAL;
+  if (p->K == 0) return TBBT_OK;
+  if (!hh_v || !hh_tau) return TBBT_EINVAL;
+  size_t es = elem_size(p->dtype);
+  if (((uintptr_t)hh_v % es) || ((uintptr_t)hh_tau % es)) return TBBT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int threads = 256;
+  const int64_t per_block = threads / 32;
+  const int64_t blocks = (p->K + per_block - 1) / per_block;
+  if (p->dtype == TBBT_COMPLEX128)
+    tbbt::relayout_kernel<zdouble><<<(unsigned)blocks, threads, 0, s>>>(
+        (const zdouble *)hh_v, (const zdouble *)hh_tau, p->d_stage_off, p->g, p->ldv, (zdouble *)p->d_store);
+  else
+    tbbt::relayout_kernel<double><<<(unsigned)blocks, threads, 0, s>>>(
+        (const double *)hh_v, (const double *)hh_tau, p->d_stage_off, p->g, p->ldv, (double *)p->d_store);
+  TBBT_CUDA_TRY(cudaGetLastError());
+  return TBBT_OK;
+}
+
+tbbt_status tbbt_plan_execute(tbbt_plan *p, void *q, int64_t ldq, void *stream) {
+  if (!p) return TBBT_EINVAL;
+  if (ldq < (p->g.n > 1 ? p->g.n : 1)) return TBBT_EINVAL;
+  if (p->nev == 0 || p->K == 0) return TBBT_OK;
+  if (!q) return TBBT_EINVAL;
+  size_t es = elem_size(p->dtype);
+  if ((uintptr_t)q % es) return TBBT_EINVAL;
+  tbbt::ApplyArgs a;
+  a.vstore = p->d_store;
+  a.q = q;
+  a.ldq = ldq;
+  a.g = p->g;
+  a.nev = p->nev;
+  a.ldv = p->ldv;
+  a.G = p->G;
+  a.NB = p->NB;
+  a.ring = p->ring;
+  a.err = p->d_err;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned blocks = (unsigned)((p->nev + 31) / 32);
+  if (p->dtype == TBBT_COMPLEX128)
+    tbbt::apply_kernel<zdouble><<<blocks, p->G * 32, p->smem, s>>>(a);
+  else
+    tbbt::apply_kernel<double><<<blocks, p->G * 32, p->smem, s>>>(a);
+  TBBT_CUDA_TRY(cudaGetLastError());
+  return TBBT_OK;
+}
+
+tbbt_status tbbt_plan_destroy(tbbt_plan *p) {
+  if (!p) return TBBT_OK;
+  if (p->d_store || p->d_stage_off || p->d_hv || p->d_ht || p->d_q) cudaDeviceSynchronize();
+  if (p->d_store) cudaFree(p->d_store);
+  if (p->d_stage_off) cudaFree(p->d_stage_off);
+  if (p->d_hv) cudaFree(p->d_hv);
+  if (p->d_ht) cudaFree(p->d_ht);
+  if (p->d_q) cudaFree(p->d_q);
+  delete p;
+  return TBBT_OK;
+}
+
+tbbt_status tbbt_stream_check(void *stream) {
+  TBBT_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  int h = 0;
+  TBBT_CUDA_TRY(cudaMemcpyFromSymbol(&h, g_tbbt_error, sizeof(int)));
+  if (h != 0) {
+    int zero = 0;
+    TBBT_CUDA_TRY(cudaMemcpyToSymbol(g_tbbt_error, &zero, sizeof(int)));
+    return TBBT_ETIMEOUT;
+  }
+  return TBBT_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// one-shot calls: plans cached by shape
+// ---------------------------------------------------------------------------
+namespace {
+std::mutex g_cache_mu;
+std::map<std::tuple<int, int64_t, int64_t, int64_t>, tbbt_plan *> g_cache;
+
+tbbt_status cached_plan(tbbt_dtype dt, int64_t n, int64_t nbw, int64_t nev, tbbt_plan **out) {
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  auto key = std::make_tuple((int)dt, n, nbw, nev);
+  auto it = g_cache.find(key);
+  if (it != g_cache.end()) {
+    *out = it->second;
+    return TBBT_OK;
+  }
+  tbbt_plan *p = nullptr;
+  tbbt_status st = tbbt_plan_create(&p, dt, n, nbw, nev, nullptr);
+  if (st != TBBT_OK) return st;
+  g_cache[key] = p;
+  *out = p;
+  return TBBT_OK;
+}
+
+tbbt_status one_shot(tbbt_dtype dt, const void *hh_v, const void *hh_tau, int64_t n, int64_t nbw, int64_t nev,
+                     void *q, int64_t ldq, void *stream) {
+  tbbt_status st = check_shape(n, nbw, nev);
+  if (st != TBBT_OK) return st;
+  if (ldq < (n > 1 ? n : 1)) return TBBT_EINVAL;
+  if (nev > 0 && n > 0 && !q) return TBBT_EINVAL;
+  if (nev == 0) return TBBT_OK;
+  tbbt_plan *p = nullptr;
+  st = cached_plan(dt, n, nbw, nev, &p);
+  if (st != TBBT_OK) return st;
+  st = tbbt_plan_set_reflectors(p, hh_v, hh_tau, stream);
+  if (st != TBBT_OK) return st;
+  return tbbt_plan_execute(p, q, ldq, stream);
+}
+
+tbbt_status one_shot_host(tbbt_dtype dt, const void *hh_v, const void *hh_tau, int64_t n, int64_t nbw,
+                          int64_t nev, void *q, int64_t ldq, void *stream) {
+  tbbt_status st = check_shape(n, nbw, nev);
+  if (st != TBBT_OK) return st;
+  if (ldq < (n > 1 ? n : 1)) return TBBT_EINVAL;
+  if (nev == 0) return TBBT_OK;
+  if (!q) return TBBT_EINVAL;
+  tbbt_plan *p = nullptr;
+  st = cached_plan(dt, n, nbw, nev, &p);
+  if (st != TBBT_OK) return st;
+  const size_t es = elem_size(dt);
+  cudaStream_t s = (cudaStream_t)stream;
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    if (p->K > 0 && !p->d_hv) {
+      TBBT_CUDA_TRY(cudaMalloc(&p->d_hv, (size_t)p->K * nbw * es));
+      TBBT_CUDA_TRY(cudaMalloc(&p->d_ht, (size_t)p->K * es));
+    }
+    if (!p->d_q) {
+      TBBT_CUDA_TRY(cudaMalloc(&p->d_q, (size_t)n * nev * es));
+      p->d_q_ld = n;
+    }
+  }
+  if (p->K > 0) {
+    if (!hh_v || !hh_tau) return TBBT_EINVAL;
+    TBBT_CUDA_TRY(cudaMemcpyAsync(p->d_hv, hh_v, (size_t)p->K * nbw * es, cudaMemcpyHostToDevice, s));
+    TBBT_CUDA_TRY(cudaMemcpyAsync(p->d_ht, hh_tau, (size_t)p->K * es, cudaMemcpyHostToDevice, s));
+  }
+  TBBT_CUDA_TRY(cudaMemcpy2DAsync(p->d_q, (size_t)n * es, q, (size_t)ldq * es, (size_t)n * es, (size_t)nev,
+                                  cudaMemcpyHostToDevice, s));
+  st = tbbt_plan_set_reflectors(p, p->d_hv, p->d_ht, stream);
+  if (st != TBBT_OK) return st;
+  st = tbbt_plan_execute(p, p->d_q, n, stream);
+  if (st != TBBT_OK) return st;
+  TBBT_CUDA_TRY(cudaMemcpy2DAsync(q, (size_t)ldq * es, p->d_q, (size_t)n * es, (size_t)n * es, (size_t)nev,
+                                  cudaMemcpyDeviceToHost, s));
+  return TBBT_OK;
+}
+}  // namespace
+
+extern "C" {
+
+tbbt_status tbbt_trans_ev_tridi_to_band_d(const double *hh_v, const double *hh_tau, int64_t n, int64_t nbw,
+                                          int64_t nev, double *q, int64_t ldq, void *stream) {
+  return one_shot(TBBT_REAL64, hh_v, hh_tau, n, nbw, nev, q, ldq, stream);
+}
+
+tbbt_status tbbt_trans_ev_tridi_to_band_z(const void *hh_v, const void *hh_tau, int64_t n, int64_t nbw,
+                                          int64_t nev, void *q, int64_t ldq, void *stream) {
+  return one_shot(TBBT_COMPLEX128, hh_v, hh_tau, n, nbw, nev, q, ldq, stream);
+}
+
+tbbt_status tbbt_trans_ev_tridi_to_band_host_d(const double *hh_v, const double *hh_tau, int64_t n,
+                                               int64_t nbw, int64_t nev, double *q, int64_t ldq, void *stream) {
+  return one_shot_host(TBBT_REAL64, hh_v, hh_tau, n, nbw, nev, q, ldq, stream);
+}
+
+tbbt_status tbbt_trans_ev_tridi_to_band_host_z(const void *hh_v, const void *hh_tau, int64_t n, int64_t nbw,
+                                               int64_t nev, void *q, int64_t ldq, void *stream) {
+  return one_shot_host(TBBT_COMPLEX128, hh_v, hh_tau, n, nbw, nev, q, ldq, stream);
+}
+
+tbbt_status tbbt_release_cache(void) {
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  for (auto &kv : g_cache) tbbt_plan_destroy(kv.second);
+  g_cache.clear();
+  return TBBT_OK;
+}
+
+}  // extern "C"
