@@ -120,9 +120,17 @@ typedef struct {
    * 0 = choose automatically. */
   int32_t sweeps_per_block;
   /* Stages each warp applies between two block-wide synchronisations;
-   * 0 = choose automatically. */
+   * 0 = choose automatically (at most 4 * sweeps_per_block). */
   int32_t stages_per_step;
-  int32_t reserved[6];
+  /* Limit of every in-kernel wait, in milliseconds; 0 = 20000. A wait that
+   * runs out records TBBT_ETIMEOUT (see tbbt_stream_check); the kernel then
+   * abandons the dependent work and exits. */
+  int32_t wait_timeout_ms;
+  /* Test hook; 0 = off. Otherwise 1 + the index of a work unit (32-column
+   * strip, group of sweeps) whose progress is never published, so that the
+   * units waiting for it run into wait_timeout_ms. */
+  int32_t debug_withhold_unit_plus1;
+  int32_t reserved[4];
 } tbbt_options;
 
 /* Creates a plan for problems of the given type and shape (arguments as for
@@ -149,7 +157,9 @@ tbbt_status tbbt_plan_info(const tbbt_plan *plan, int32_t *sweeps_per_block, int
                            int32_t *ring_rows, int32_t *smem_bytes, int32_t *blocks);
 
 /* Synchronises `stream`, then reports (and clears) the device error word:
- * TBBT_OK, TBBT_ETIMEOUT, or TBBT_ECUDA if the stream itself failed. */
+ * TBBT_OK, TBBT_ETIMEOUT, or TBBT_ECUDA if the stream itself failed. The
+ * word is sticky: after a timeout, later launches return at once without
+ * computing until this call has cleared it. */
 tbbt_status tbbt_stream_check(void *stream);
 
 /* Host-side check of the block schedule (no GPU needed): largest number of

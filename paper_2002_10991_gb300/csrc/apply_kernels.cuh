@@ -135,6 +135,15 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // ---------------------------------------------------------------------------
 // the apply kernel
 // ---------------------------------------------------------------------------
+// Work is split into units (strip of 32 columns, epoch of G sweeps), claimed
+// by persistent blocks from an atomic counter in epoch-major order. Epoch e
+// of a strip reads the rows epoch e-1 has finished; instead of waiting for the
+// whole epoch, it follows it down the column: epoch e-1 publishes after
+// every step the lowest row it has written back for good ("released"), and
+// epoch e waits (bounded) until the rows it is about to load are released.
+// A unit only ever waits for a unit with a smaller index, which was claimed
+// earlier by a block that is already running, so the pipeline cannot
+// deadlock, and all SMs stay busy even when the strips are fewer than SMs.
 struct ApplyArgs {
   const void *vstore;  // sweep-major store, ldv elements per reflector
   void *q;
@@ -142,32 +151,112 @@ struct ApplyArgs {
   StoreGeom g;
   int32_t nev;
   int32_t ldv;
-  int32_t G;     // sweeps (warps) per block
-  int32_t NB;    // stages per step
-  int32_t ring;  // rows in the shared-memory ring
+  int32_t G;       // sweeps (warps) per block
+  int32_t NB;      // stages per step
+  int32_t ring;    // rows in the shared-memory ring
+  int32_t strips;  // ceil(nev / 32)
+  int32_t units;   // strips * epochs
+  int *flags;      // per unit: lowest released row (INT_MAX at start), kPoison if abandoned
+  unsigned *counter;
   int *err;
+  long long timeout_ns;
+  int withhold;  // test hook: unit whose progress is never published (-1: none)
 };
 
-// Rows [r0, r1) of the strip: global -> ring (cp.async). Columns >= nev are
-// zero-filled so that idle lanes compute on zeros.
+constexpr int kPoison = -2;
+constexpr int kMaxPrefetch = 4;  // rows-per-step * 32 <= kMaxPrefetch * threads
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int *p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ long long globaltimer_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+
+// Bounded wait until the unit behind `flag` has released every row >= need.
+// Returns 0 when it has, 1 if the producer was abandoned, an error was
+// recorded elsewhere, or the wait timed out (which it records).
+__device__ int wait_released(const ApplyArgs &a, const int *flag, int need) {
+  long long t0 = globaltimer_ns();
+  for (unsigned it = 0;; ++it) {
+    int v = ld_acquire(flag);
+    if (v == kPoison) return 1;
+    if (v <= need) return 0;
+    if (*(volatile int *)a.err != 0) return 1;
+    if (globaltimer_ns() - t0 > a.timeout_ns) {
+      atomicCAS(a.err, 0, 4 /* TBBT_ETIMEOUT */);
+      return 1;
+    }
+    __nanosleep(it < 64 ? 64 : 512);
+  }
+}
+
 template <typename T>
-__device__ __forceinline__ void load_rows(const ApplyArgs &a, T *ring, int32_t r0, int32_t r1, int32_t c0) {
+__device__ __forceinline__ T ld_cg(const T *p);
+template <>
+__device__ __forceinline__ double ld_cg<double>(const double *p) {
+  return __ldcg(p);
+}
+template <>
+__device__ __forceinline__ zdouble ld_cg<zdouble>(const zdouble *p) {
+  double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
+  return zdouble{v.x, v.y};
+}
+
+// Rows [r0, r1) of the strip, global -> ring, synchronously (L2 path: rows
+// may have been written by another SM). Columns >= nev read as zero.
+template <typename T>
+__device__ __forceinline__ void load_rows_now(const ApplyArgs &a, T *ring, int32_t r0, int32_t r1, int32_t c0) {
   const int32_t nrows = r1 - r0;
   if (nrows <= 0) return;
   const T *q = reinterpret_cast<const T *>(a.q);
-  const int32_t total = nrows * 32;
-  for (int32_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
+  for (int32_t idx = threadIdx.x; idx < nrows * 32; idx += blockDim.x) {
     int32_t c = idx / nrows;
     int32_t r = r0 + (idx - c * nrows);
-    T *dst = ring + (int64_t)(r % a.ring) * 32 + c;
     int32_t col = c0 + c;
-    if (col < a.nev) {
-      cp_async<sizeof(T)>(dst, q + (int64_t)col * a.ldq + r);
-    } else {
-      *dst = Arith<T>::zero();
-    }
+    ring[(int64_t)(r % a.ring) * 32 + c] = col < a.nev ? ld_cg(q + (int64_t)col * a.ldq + r) : Arith<T>::zero();
   }
 }
+
+// The same split in two: issue the loads into registers now, write them to
+// the ring after the step's arithmetic (hides the memory latency).
+template <typename T>
+struct RowPrefetch {
+  T val[kMaxPrefetch];
+  __device__ __forceinline__ void issue(const ApplyArgs &a, int32_t r0, int32_t r1, int32_t c0) {
+    const int32_t nrows = r1 - r0;
+    const T *q = reinterpret_cast<const T *>(a.q);
+#pragma unroll
+    for (int i = 0; i < kMaxPrefetch; ++i) {
+      int32_t idx = threadIdx.x + i * blockDim.x;
+      if (nrows > 0 && idx < nrows * 32) {
+        int32_t c = idx / nrows;
+        int32_t r = r0 + (idx - c * nrows);
+        int32_t col = c0 + c;
+        val[i] = col < a.nev ? ld_cg(q + (int64_t)col * a.ldq + r) : Arith<T>::zero();
+      }
+    }
+  }
+  __device__ __forceinline__ void commit(const ApplyArgs &a, T *ring, int32_t r0, int32_t r1) {
+    const int32_t nrows = r1 - r0;
+#pragma unroll
+    for (int i = 0; i < kMaxPrefetch; ++i) {
+      int32_t idx = threadIdx.x + i * blockDim.x;
+      if (nrows > 0 && idx < nrows * 32) {
+        int32_t c = idx / nrows;
+        int32_t r = r0 + (idx - c * nrows);
+        ring[(int64_t)(r % a.ring) * 32 + c] = val[i];
+      }
+    }
+  }
+};
 
 // Rows [r0, r1): ring -> global.
 template <typename T>
@@ -184,7 +273,8 @@ __device__ __forceinline__ void store_rows(const ApplyArgs &a, const T *ring, in
   }
 }
 
-// Reflector entries of warp w for its block at step t -> its buffer slot.
+// Reflector entries of warp w for its block at step t -> its buffer slot
+// (read-only data: asynchronous copies, completed by wait_all + barrier).
 template <typename T>
 __device__ __forceinline__ void load_reflectors(const ApplyArgs &a, const Epoch &ep, T *vbuf_w, int32_t w,
                                                 int32_t t, int lane) {
@@ -195,7 +285,6 @@ __device__ __forceinline__ void load_reflectors(const ApplyArgs &a, const Epoch 
   const int32_t sig = ep.sig_top - (t - w) * ep.nb;
   const T *src = reinterpret_cast<const T *>(a.vstore) + (a.g.sweep_offset(j) + (a.g.imax(j) - hi)) * a.ldv;
   T *dst = vbuf_w + (int64_t)(t & 1) * ep.nb * a.ldv + (int64_t)(sig - hi) * a.ldv;
-  // (hi - lo + 1) * ldv elements, contiguous on both sides, 16-byte chunks
   const int32_t nchunks = (hi - lo + 1) * a.ldv * (int32_t)sizeof(T) / 16;
   const char *s8 = reinterpret_cast<const char *>(src);
   char *d8 = reinterpret_cast<char *>(dst);
@@ -234,54 +323,87 @@ __device__ __forceinline__ void apply_one(T *col, int32_t ring, int32_t r, int32
 template <typename T>
 __global__ void __launch_bounds__(512, 1) apply_kernel(ApplyArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_unit;
+  __shared__ int s_stop;
   T *ring = reinterpret_cast<T *>(smem_raw);
   T *vbuf = ring + (int64_t)a.ring * 32;
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
-  const int32_t c0 = blockIdx.x * 32;
   const StoreGeom &g = a.g;
-  const int32_t J = g.num_sweeps();
   T *vbuf_w = vbuf + (int64_t)w * 2 * a.NB * a.ldv;
   T *mycol = ring + lane;
 
-  for (int32_t e = 0; e * a.G < J; ++e) {
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_unit = (int)atomicAdd(a.counter, 1u);
+      s_stop = (*(volatile int *)a.err != 0);
+    }
+    __syncthreads();
+    const int u = s_unit;
+    if (u >= a.units || s_stop) break;
+    const int32_t e = u / a.strips;
+    const int32_t c0 = (u - e * a.strips) * 32;
+    int *myflag = a.flags + u;
+    const int *prevflag = e > 0 ? a.flags + (u - a.strips) : nullptr;
     const Epoch ep = make_epoch(g, e, a.G, a.NB);
+
     // prologue: rows needed at step 0 and the reflectors of step 0
     int32_t top = step_min_row(g, ep, 0);
-    load_rows<T>(a, ring, top, g.n, c0);
-    load_reflectors<T>(a, ep, vbuf_w, w, 0, lane);
-    cp_async_wait_all();
+    if (threadIdx.x == 0) s_stop = prevflag ? wait_released(a, prevflag, top) : 0;
     __syncthreads();
-    int32_t released = g.n;  // rows >= released are back in global memory
-    for (int32_t t = 0; t < ep.nsteps; ++t) {
-      // rows no warp touches from step t on
-      int32_t live = rows_live_max(g, ep, t);
-      int32_t rel = live + 1 > top ? live + 1 : top;
-      if (rel < released) {
-        store_rows<T>(a, ring, rel, released, c0);
-        released = rel;
-      }
-      // prefetch rows and reflectors of step t+1
-      int32_t ntop = step_min_row(g, ep, t + 1);
-      load_rows<T>(a, ring, ntop, top, c0);
-      top = ntop;
-      load_reflectors<T>(a, ep, vbuf_w, w, t + 1, lane);
-      // apply this warp's stages of step t
-      int32_t hi, lo;
-      warp_stages(g, ep, w, t, &hi, &lo);
-      if (hi >= lo) {
-        const int32_t j = ep.j0 + w;
-        const int32_t sig = ep.sig_top - (t - w) * ep.nb;
-        const T *vb = vbuf_w + (int64_t)(t & 1) * ep.nb * a.ldv;
-        for (int32_t s = hi; s >= lo; --s) {
-          apply_one<T>(mycol, a.ring, g.row(s, j), g.len(s, j), vb + (int64_t)(sig - s) * a.ldv);
-        }
-      }
+    bool abandoned = s_stop != 0;
+    if (!abandoned) {
+      load_rows_now<T>(a, ring, top, g.n, c0);
+      load_reflectors<T>(a, ep, vbuf_w, w, 0, lane);
       cp_async_wait_all();
       __syncthreads();
+      int32_t released = g.n;  // rows >= released are back in global memory
+      RowPrefetch<T> pf;
+      for (int32_t t = 0; t < ep.nsteps; ++t) {
+        // rows no warp touches from step t on go back to global memory
+        int32_t live = rows_live_max(g, ep, t);
+        int32_t rel = live + 1 > top ? live + 1 : top;
+        if (rel < released) {
+          store_rows<T>(a, ring, rel, released, c0);
+          released = rel;
+        }
+        // rows of step t+1 must have been released by the previous epoch
+        const int32_t ntop = step_min_row(g, ep, t + 1);
+        if (threadIdx.x == 0) s_stop = (prevflag && ntop < top) ? wait_released(a, prevflag, ntop) : 0;
+        __syncthreads();
+        if (s_stop) {
+          abandoned = true;
+          break;
+        }
+        if (threadIdx.x == 0 && u != a.withhold) st_release(myflag, released);
+        pf.issue(a, ntop, top, c0);
+        load_reflectors<T>(a, ep, vbuf_w, w, t + 1, lane);
+        // this warp's stages of step t
+        int32_t hi, lo;
+        warp_stages(g, ep, w, t, &hi, &lo);
+        if (hi >= lo) {
+          const int32_t j = ep.j0 + w;
+          const int32_t sig = ep.sig_top - (t - w) * ep.nb;
+          const T *vb = vbuf_w + (int64_t)(t & 1) * ep.nb * a.ldv;
+          for (int32_t s = hi; s >= lo; --s)
+            apply_one<T>(mycol, a.ring, g.row(s, j), g.len(s, j), vb + (int64_t)(sig - s) * a.ldv);
+        }
+        pf.commit(a, ring, ntop, top);
+        top = ntop;
+        cp_async_wait_all();
+        __syncthreads();
+      }
+      if (!abandoned) {
+        // the rest of the strip is final for this epoch
+        store_rows<T>(a, ring, top, released, c0);
+        __syncthreads();
+        if (threadIdx.x == 0 && u != a.withhold) st_release(myflag, top);
+      }
     }
-    // flush the rows still resident
-    store_rows<T>(a, ring, top, released, c0);
+    if (abandoned) {
+      cp_async_wait_all();
+      if (threadIdx.x == 0) st_release(myflag, kPoison);
+    }
     __syncthreads();
   }
 }

@@ -66,6 +66,12 @@ struct tbbt_plan {
   void *d_store = nullptr;       // re-laid reflectors, K * ldv elements
   int64_t *d_stage_off = nullptr;  // n entries
   int *d_err = nullptr;
+  // persistent apply kernel: one progress flag per (strip, epoch) unit
+  int32_t strips = 0, epochs = 0, units = 0, grid = 0;
+  int *d_flags = nullptr;
+  unsigned *d_counter = nullptr;
+  long long timeout_ns = 20000000000LL;
+  int withhold = -1;
   // device copies used by the host-buffer entry points (allocated on demand)
   void *d_hv = nullptr, *d_ht = nullptr, *d_q = nullptr;
   int64_t d_q_ld = 0;
@@ -161,6 +167,7 @@ tbbt_status tbbt_plan_create(tbbt_plan **plan, tbbt_dtype dtype, int64_t n, int6
   int32_t wantNB = opt && opt->stages_per_step > 0 ? opt->stages_per_step : 8;
   if (wantG > 16) wantG = 16;
   int32_t G = wantG, NB = wantNB;
+  if (NB > 4 * G) NB = 4 * G;  // the row prefetch holds at most 4 elements per thread
   while (smem_bytes_for(dtype, (int32_t)nbw, G, NB) > (size_t)kMaxSmem) {
     if (G > 4 || (NB <= 2 && G > 1))
       --G;
@@ -177,6 +184,11 @@ tbbt_status tbbt_plan_create(tbbt_plan **plan, tbbt_dtype dtype, int64_t n, int6
   p->NB = NB;
   p->ring = ring_rows_for((int32_t)nbw, G, NB);
   p->smem = smem_bytes_for(dtype, (int32_t)nbw, G, NB);
+  if (opt && opt->wait_timeout_ms > 0) p->timeout_ns = (long long)opt->wait_timeout_ms * 1000000LL;
+  if (opt && opt->debug_withhold_unit_plus1 > 0) p->withhold = opt->debug_withhold_unit_plus1 - 1;
+  p->strips = (int32_t)((nev + 31) / 32);
+  p->epochs = (p->g.num_sweeps() + G - 1) / G;
+  p->units = p->strips * p->epochs;
 
   auto fail = [&](tbbt_status s) {
     tbbt_plan_destroy(p);
@@ -211,6 +223,25 @@ tbbt_status tbbt_plan_create(tbbt_plan **plan, tbbt_dtype dtype, int64_t n, int6
   else
     e = cudaFuncSetAttribute(tbbt::apply_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
   if (e != cudaSuccess) return fail(TBBT_ECUDA);
+  if (p->units > 0) {
+    e = cudaMalloc(&p->d_flags, sizeof(int) * (size_t)p->units);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_counter, sizeof(unsigned));
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      return fail(TBBT_ENOMEM);
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return fail(TBBT_ECUDA);
+    if (dtype == TBBT_COMPLEX128)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tbbt::apply_kernel<zdouble>, G * 32, p->smem);
+    else
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tbbt::apply_kernel<double>, G * 32, p->smem);
+    if (e != cudaSuccess || per_sm < 1) return fail(TBBT_ECUDA);
+    int64_t resident = (int64_t)sms * per_sm;
+    p->grid = (int32_t)(p->units < resident ? p->units : resident);
+  }
   *plan = p;
   return TBBT_OK;
 }
@@ -222,7 +253,7 @@ tbbt_status tbbt_plan_info(const tbbt_plan *p, int32_t *G, int32_t *NB, int32_t 
   if (NB) *NB = p->NB;
   if (ring) *ring = p->ring;
   if (smem) *smem = (int32_t)p->smem;
-  if (blocks) *blocks = (p->nev + 31) / 32;
+  if (blocks) *blocks = p->grid;
   return TBBT_OK;
 }
 
@@ -263,9 +294,17 @@ tbbt_status tbbt_plan_execute(tbbt_plan *p, void *q, int64_t ldq, void *stream) 
   a.G = p->G;
   a.NB = p->NB;
   a.ring = p->ring;
+  a.strips = p->strips;
+  a.units = p->units;
+  a.flags = p->d_flags;
+  a.counter = p->d_counter;
   a.err = p->d_err;
+  a.timeout_ns = p->timeout_ns;
+  a.withhold = p->withhold;
   cudaStream_t s = (cudaStream_t)stream;
-  unsigned blocks = (unsigned)((p->nev + 31) / 32);
+  TBBT_CUDA_TRY(cudaMemsetAsync(p->d_flags, 0x7f, sizeof(int) * (size_t)p->units, s));
+  TBBT_CUDA_TRY(cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned), s));
+  unsigned blocks = (unsigned)p->grid;
   if (p->dtype == TBBT_COMPLEX128)
     tbbt::apply_kernel<zdouble><<<blocks, p->G * 32, p->smem, s>>>(a);
   else
@@ -276,9 +315,11 @@ tbbt_status tbbt_plan_execute(tbbt_plan *p, void *q, int64_t ldq, void *stream) 
 
 tbbt_status tbbt_plan_destroy(tbbt_plan *p) {
   if (!p) return TBBT_OK;
-  if (p->d_store || p->d_stage_off || p->d_hv || p->d_ht || p->d_q) cudaDeviceSynchronize();
+  if (p->d_store || p->d_stage_off || p->d_flags || p->d_hv || p->d_ht || p->d_q) cudaDeviceSynchronize();
   if (p->d_store) cudaFree(p->d_store);
   if (p->d_stage_off) cudaFree(p->d_stage_off);
+  if (p->d_flags) cudaFree(p->d_flags);
+  if (p->d_counter) cudaFree(p->d_counter);
   if (p->d_hv) cudaFree(p->d_hv);
   if (p->d_ht) cudaFree(p->d_ht);
   if (p->d_q) cudaFree(p->d_q);
