@@ -1,0 +1,354 @@
+"""Benchmark of the tridiagonal -> band eigenvector back-transformation (Eq. 6d).
+
+Workload: real symmetric, n = 8192, semi-bandwidth 64, nev = 4096 lowest
+eigenvectors (the paper's plain FP64 method at a DFT-like size). One step =
+the whole hot path on one batch: re-lay the reflector store (K = 528,128
+reflectors) and apply it to the 8192 x 4096 eigenvector block. Inputs are
+seeded and synthetic (unitary Householder reflectors with the exact store
+geometry, N(0, 1/n) eigenvector block); both exceed the 129 MB L2.
+
+Metric: algorithmic TFLOP/s = 4 * nev * sum_k L_k flops per step (Eq. 8:
+a length-L dot product and a length-L update per reflector and column)
+divided by device time. Roofline: the apply kernel is FP64-ALU bound
+(arithmetic intensity ~700 flop/byte, far above the FP64 ridge of ~0.2).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU (torchrun): every rank runs an independent replica (the columns
+of an eigenvector block are independent; no data-path collective).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2002_10991_gb300 import inputs as I  # noqa: E402
+
+METRIC = "eigvec back-transform TFLOP/s,% FP64 peak; mixed vs FP64 speedup at set resid"
+WORKLOAD = "real-n8192-b64-dft"
+
+# FP64 peak of a GB300: 152 SMs x 2 DFMA per clock x 2 flops at the 2070 MHz
+# maximum SM clock (a DFMA microbenchmark measured 1.198 TFLOP/s at ~2000 MHz,
+# i.e. the same 2 DFMA/clock/SM).
+SMS, DFMA_PER_CLK_SM, SM_MAX_MHZ = 152, 2, 2070.0
+FP64_PEAK_TFLOPS = SMS * DFMA_PER_CLK_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+# DRAM bytes (read + write) of one apply-kernel launch on this workload, from
+# the ncu capture summarised in profiles/, valid for the kernel sources whose
+# hash is recorded beside it (reported as null otherwise).
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "apply_kernel_traffic.json")
+
+
+def set_workload(name: str):
+    global WORKLOAD
+    if name not in I.WORKLOADS or I.WORKLOADS[name]["complex_"]:
+        raise SystemExit(f"unknown or unsupported workload {name}")
+    WORKLOAD = name
+
+
+def csrc_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2002_10991_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    try:
+        rec = json.load(open(TRAFFIC_FILE))
+    except Exception:
+        return None
+    if rec.get("csrc_hash") != csrc_hash():
+        return None
+    return rec.get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload_inputs(name: str):
+    w = I.WORKLOADS[name]
+    n, b, nev, cplx = w["n"], w["b"], w["nev"], w["complex_"]
+    v, tau = I.synthetic_store(n, b, w["seed"], cplx)
+    X = I.eigvec_block(n, nev, w["seed"], cplx)
+    sum_l = int(I.store_lengths(n, b, cplx).sum())
+    flops = (16 if cplx else 4) * nev * sum_l
+    return w, v, tau, X, sum_l, flops
+
+
+def cpu_sample(v, tau, X, w, ncols: int, seed: int = 1):
+    """Columns of the workload the oracle back-transforms on the host."""
+    rng = np.random.default_rng(seed)
+    cols = np.sort(rng.choice(w["nev"], size=min(ncols, w["nev"]), replace=False))
+    return cols, np.asfortranarray(X[:, cols])
+
+
+def run_oracle_sample(v, tau, w, Xs):
+    import oracle
+
+    cores = oracle.num_cpus()
+    Z = Xs.copy(order="F")
+    t0 = time.perf_counter()
+    oracle.back_transform(v, tau, w["n"], w["b"], Z, nthreads=cores)
+    return Z, time.perf_counter() - t0, cores
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reference_arm(args, world, rank):
+    """The oracle timed on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    w, v, tau, X, sum_l, flops_full = workload_inputs(WORKLOAD)
+    ncols = args.ref_cols
+    cols, Xs = cpu_sample(v, tau, X, w, ncols)
+    fl = 4 * len(cols) * sum_l
+    for _ in range(args.warmup_ref):
+        run_oracle_sample(v, tau, w, Xs)
+    times, cores = [], 1
+    for _ in range(args.steps):
+        _, dt, cores = run_oracle_sample(v, tau, w, Xs)
+        times.append(dt)
+    total = sum(times)
+    value = fl * len(times) / total / 1e12
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup_ref, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(w, "host cores; oracle sample"),
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{len(cols)} of {w['nev']} columns, all {len(tau)} reflectors, per step"},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(w, note=""):
+    return {"workload": WORKLOAD, "n": w["n"], "nbw": w["b"], "nev": w["nev"], "dtype": "real64",
+            "store": "seeded synthetic unitary reflectors, canonical store layout",
+            "x": "seeded N(0,1/n) eigenvector block",
+            "l2": f"inputs larger than L2 (q {w['n'] * w['nev'] * 8 / 1e6:.0f} MB, store "
+                  f"{I.store_lengths(w['n'], w['b'], False).size * w['b'] * 8 / 1e6:.0f} MB)",
+            "parallelism": "replicas", "note": note}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-cols", type=int, default=512, help="columns in the CPU-baseline sample")
+    ap.add_argument("--ref-cols", type=int, default=256, help="columns per step of the reference arm")
+    ap.add_argument("--warmup-ref", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="named workload (default: the benchmark workload; others are for profiler captures)")
+    args = ap.parse_args()
+    set_workload(args.workload)
+    world, rank, local = dist_setup()
+
+    if args.impl == "reference":
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.init_process_group("gloo")
+        reference_arm(args, world, rank)
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+        return
+
+    import torch
+
+    import paper_2002_10991_gb300 as P
+    from paper_2002_10991_gb300 import _native
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _native.load()  # the library must be built (fails loudly otherwise)
+
+    w, v, tau, X, sum_l, flops = workload_inputs(WORKLOAD)
+    n, b, nev = w["n"], w["b"], w["nev"]
+    dv = torch.from_numpy(v).cuda()
+    dt = torch.from_numpy(tau).cuda()
+    q = torch.from_numpy(X.T.copy()).cuda().t()
+    stream = torch.cuda.current_stream()
+    plan = P.Plan(False, n, b, nev)
+    info = plan.info()
+
+    # parity pass on the pristine block (columns checked by the CPU baseline)
+    cols, Xs = cpu_sample(v, tau, X, w, args.cpu_cols)
+    plan.set_reflectors(dv, dt)
+    plan.execute(q)
+    P.stream_check()
+    gpu_cols = q[:, torch.from_numpy(cols).cuda()].cpu().numpy()
+
+    for _ in range(args.warmup):
+        plan.set_reflectors(dv, dt)
+        plan.execute(q)
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        t_begin = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_begin.record(stream)
+        for k in range(args.steps):
+            a, m, z = ev[k]
+            a.record(stream)
+            plan.set_reflectors(dv, dt)
+            m.record(stream)
+            plan.execute(q)
+            z.record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    P.stream_check()
+    total_ms = t_begin.elapsed_time(t_end)
+    apply_ms = [m.elapsed_time(z) for (a, m, z) in ev]
+    relayout_ms = [a.elapsed_time(m) for (a, m, z) in ev]
+    if world > 1:
+        tt = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    value = flops * args.steps * world / (total_ms * 1e-3) / 1e12
+
+    # end to end through the host-buffer C ABI (pinned host memory, copies inside)
+    hv = torch.from_numpy(v).pin_memory()
+    ht = torch.from_numpy(tau).pin_memory()
+    hq = torch.from_numpy(X.T.copy()).pin_memory().t()
+    P.trans_ev_tridi_to_band_host(hv, ht, n, b, nev, hq)  # warm (allocates the cached copies)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        P.trans_ev_tridi_to_band_host(hv, ht, n, b, nev, hq, synchronize=False)
+    P.stream_check()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e = {"value": flops * args.e2e_steps * world / e2e_s / 1e12, "unit": "TFLOP/s",
+           "h2d_bytes_per_step": int(v.nbytes + tau.nbytes + n * nev * 8), "d2h_bytes_per_step": int(n * nev * 8),
+           "steps": args.e2e_steps, "api": "tbbt_trans_ev_tridi_to_band_host_d"}
+
+    if rank == 0:
+        apply_avg = sum(apply_ms) / len(apply_ms)
+        achieved = flops / (apply_avg * 1e-3) / 1e12
+        cs = clocks.summary()
+        peak_at_clock = None
+        if cs["sm_mhz"]:
+            peak_at_clock = SMS * DFMA_PER_CLK_SM * 2 * cs["sm_mhz"] * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": recorded_traffic(),
+                "kernel": "tbbt::apply_kernel<double>",
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe; DFMA probe 1.198 TF)",
+                "peak_at_sampled_clock": peak_at_clock,
+                "algorithmic_bytes_per_launch": int(2 * n * nev * 8 + sum_l * 8)}
+        Zo, cpu_s, cores = run_oracle_sample(v, tau, w, Xs)
+        cpu = {"value": 4 * len(cols) * sum_l / cpu_s / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+               "sample": f"{len(cols)} of {nev} columns, all {len(tau)} reflectors",
+               "parity_max_abs_vs_gpu": float(np.abs(Zo - gpu_cols).max())}
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(w),
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
+            "clocks": cs, "relayout_ms_avg": sum(relayout_ms) / len(relayout_ms), "apply_ms_avg": apply_avg,
+            "launch": info,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

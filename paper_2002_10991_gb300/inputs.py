@@ -171,7 +171,7 @@ def synthetic_store(n: int, b: int, seed: int, complex_: bool = False):
     Returns ``(hh_v, hh_tau)``: ``hh_v`` is K x b column-major (reflector k is
     the contiguous slice ``hh_v[k*b:(k+1)*b]``) with ``v[0] = 1`` stored and
     zeros at positions >= L_k; ``hh_tau`` has K entries. Entries v[1:L] are
-    N(0, 1/L) draws; tau is chosen so that I - tau v v^H is unitary:
+    N(0, 1/b) draws; tau is chosen so that I - tau v v^H is unitary:
     tau = 2/|v|^2 for real data and tau = (1 - exp(i*theta))/|v|^2 with
     theta ~ U[0, 2pi) for complex data. Used where the stores of real
     reductions are too slow to produce on the host; the back-transform's cost
@@ -206,6 +206,8 @@ WORKLOADS = {
     "real-n8192-b64-dft": dict(n=8192, b=64, nev=4096, complex_=False, kind="dft", seed=SEED_BASE + 2),
     "complex-n20000-b64-dft": dict(n=20000, b=64, nev=6000, complex_=True, kind="dft", seed=SEED_BASE + 3),
     "real-n32768-b64-dft": dict(n=32768, b=64, nev=9830, complex_=False, kind="dft", seed=SEED_BASE + 4),
+    # a smaller case of the same kernel for profiler captures (q still larger than L2)
+    "real-n4096-b64-dft": dict(n=4096, b=64, nev=4096, complex_=False, kind="dft", seed=SEED_BASE + 6),
 }
 
 
