@@ -21,7 +21,10 @@ using tbbt::zdouble;
 namespace {
 
 constexpr int32_t kMaxBand = 128;
-constexpr int32_t kMaxSmem = 227 * 1024;
+// Dynamic shared memory a launch may use: the 227 KB opt-in limit of a block
+// covers static plus dynamic shared memory, so leave 1 KB for the kernels'
+// static variables.
+constexpr int32_t kMaxSmem = 226 * 1024;
 
 #define TBBT_CUDA_TRY(expr)                          \
   do {                                               \
@@ -36,6 +39,21 @@ constexpr int32_t kMaxSmem = 227 * 1024;
 __device__ int g_tbbt_error = 0;
 
 int32_t round_even(int32_t b) { return (b + 1) & ~1; }
+
+// Raise the kernel's dynamic shared memory limit to what the device allows
+// beside its static shared memory (at least kMaxSmem on sm_103).
+template <typename K>
+cudaError_t allow_max_dynamic_smem(K kernel) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  int allowed = optin - (int)fa.sharedSizeBytes;
+  if (allowed < kMaxSmem) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, allowed);
+}
 
 size_t elem_size(tbbt_dtype dt) { return dt == TBBT_COMPLEX128 ? 16 : 8; }
 
@@ -218,10 +236,13 @@ tbbt_status tbbt_plan_create(tbbt_plan **plan, tbbt_dtype dtype, int64_t n, int6
   }
   e = cudaGetSymbolAddress((void **)&p->d_err, g_tbbt_error);
   if (e != cudaSuccess) return fail(TBBT_ECUDA);
+  // The attribute belongs to the kernel, not to the plan: raise it to the
+  // largest size any plan may use, so that creating a plan with a smaller
+  // footprint never invalidates the launches of an earlier, larger one.
   if (dtype == TBBT_COMPLEX128)
-    e = cudaFuncSetAttribute(tbbt::apply_kernel<zdouble>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
+    e = allow_max_dynamic_smem(tbbt::apply_kernel<zdouble>);
   else
-    e = cudaFuncSetAttribute(tbbt::apply_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem);
+    e = allow_max_dynamic_smem(tbbt::apply_kernel<double>);
   if (e != cudaSuccess) return fail(TBBT_ECUDA);
   if (p->units > 0) {
     e = cudaMalloc(&p->d_flags, sizeof(int) * (size_t)p->units);

@@ -161,6 +161,25 @@ def test_plan_reuse_with_new_reflectors(P):
     plan.close()
 
 
+def test_smaller_plan_does_not_break_earlier_plan(P):
+    # plans share the kernel; a later plan with less shared memory must not
+    # invalidate the launch configuration of an earlier one
+    n, b, nev = 400, 64, 40
+    big = P.Plan(False, n, b, nev)
+    small = P.Plan(False, 100, 4, 10, sweeps_per_block=1, stages_per_step=1)
+    assert big.info()["smem_bytes"] > small.info()["smem_bytes"]
+    v, tau = I.synthetic_store(n, b, 31, False)
+    X = I.eigvec_block(n, nev, 32, False)
+    big.set_reflectors(dev(v), dev(tau))
+    q = torch.from_numpy(X.T.copy()).cuda().t()
+    big.execute(q)
+    P.stream_check()
+    Zo = oracle.back_transform(v, tau, n, b, X.copy(order="F"))
+    assert maxdiff(q.cpu().numpy(), Zo) <= TOL
+    big.close()
+    small.close()
+
+
 @pytest.mark.parametrize("cplx", [False, True])
 def test_host_buffer_entry_point_matches_device_path(P, cplx):
     n, b, nev = 600, 64, 90
