@@ -162,6 +162,35 @@ tbbt_status tbbt_plan_info(const tbbt_plan *plan, int32_t *sweeps_per_block, int
  * computing until this call has cleared it. */
 tbbt_status tbbt_stream_check(void *stream);
 
+/* ---------------------------------------------------------------------------
+ * The same computation without any allocation (the paper has no counterpart;
+ * this is a service of the library). For callers that cannot allocate device
+ * memory when they call: all of the GPU may already belong to another
+ * allocator, the call may sit in a loop where the host-device
+ * synchronisation of cudaMalloc/cudaFree is not acceptable, or the caller
+ * must not meet out-of-memory at run time.
+ *
+ * dtype selects real (double) or Hermitian (interleaved complex double)
+ * data; the other arguments are as for tbbt_trans_ev_tridi_to_band_d/_z
+ * (device pointers, q overwritten in place). Nothing is allocated: the
+ * scratch (sweep-major copy of the store, stage offsets, progress flags) lives
+ * in one array of TBBT_NOALLOC_SCRATCH_BYTES in the library's device code,
+ * which every GPU that loads the library holds until the process exits.
+ * Problems whose scratch does not fit -- about K * round_up(nbw, 2) elements
+ * of 8 (real) or 16 (complex) bytes plus small tables, i.e. up to n ~ 2800
+ * real or ~ 2000 complex at nbw = 64 -- return TBBT_ENOTSUP before any work.
+ *
+ * The first call on each device sets that device up (looks up the array's
+ * device address, sets a kernel attribute); make that first call before any
+ * stream capture. Every call shares the one array and leaves its contents
+ * behind (the parts that must start cleared are cleared by each call), so
+ * calls that overlap on the GPU -- on different streams or from different
+ * host threads -- race and corrupt each other's results: serialise them.
+ * ------------------------------------------------------------------------- */
+#define TBBT_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+tbbt_status tbbt_trans_ev_tridi_to_band_noalloc(tbbt_dtype dtype, const void *hh_v, const void *hh_tau, int64_t n,
+                                                int64_t nbw, int64_t nev, void *q, int64_t ldq, void *stream);
+
 /* Host-side check of the block schedule (no GPU needed): largest number of
  * rows a thread block ever holds at once for these parameters, or -1 if the
  * schedule would touch a row twice in one step. Used by tests to show the

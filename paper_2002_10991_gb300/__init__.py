@@ -11,4 +11,5 @@ from .api import (  # noqa: F401
     stream_check,
     trans_ev_tridi_to_band,
     trans_ev_tridi_to_band_host,
+    trans_ev_tridi_to_band_noalloc,
 )

@@ -81,6 +81,8 @@ def load():
         L.tbbt_plan_info.argtypes = [p] + [ctypes.POINTER(i32)] * 5
         L.tbbt_stream_check.restype = c_int
         L.tbbt_stream_check.argtypes = [p]
+        L.tbbt_trans_ev_tridi_to_band_noalloc.restype = c_int
+        L.tbbt_trans_ev_tridi_to_band_noalloc.argtypes = [c_int, p, p, i64, i64, i64, p, i64, p]
         L.tbbt_schedule_max_live_rows.restype = i64
         L.tbbt_schedule_max_live_rows.argtypes = [i64, i64, c_int, i32, i32]
         _lib = L

@@ -115,6 +115,23 @@ def trans_ev_tridi_to_band_host(hh_v, hh_tau, n: int, nbw: int, nev: int, q, ldq
     return q
 
 
+def trans_ev_tridi_to_band_noalloc(hh_v, hh_tau, n: int, nbw: int, nev: int, q, ldq: int | None = None,
+                                   stream=None):
+    """The same as trans_ev_tridi_to_band, through the entry point that
+    allocates no memory (for callers that cannot allocate; its scratch is a
+    fixed 32 MiB array per device, and concurrent calls race on it). Raises
+    TbbtError (ENOTSUP) for problems whose scratch does not fit."""
+    cplx = _is_complex_dtype(q)
+    if ldq is None:
+        ldq, _ = _q_layout(q, n)
+    st = _native.load().tbbt_trans_ev_tridi_to_band_noalloc(
+        COMPLEX128 if cplx else REAL64, ctypes.c_void_p(hh_v.data_ptr() if hh_v.numel() else 0),
+        ctypes.c_void_p(hh_tau.data_ptr() if hh_tau.numel() else 0), n, nbw, nev,
+        ctypes.c_void_p(q.data_ptr() if q.numel() else 0), ldq, _stream_handle(stream))
+    _check(st, "tbbt_trans_ev_tridi_to_band_noalloc")
+    return q
+
+
 def release_cache():
     _check(_native.load().tbbt_release_cache(), "tbbt_release_cache")
 

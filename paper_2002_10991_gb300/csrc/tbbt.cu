@@ -470,3 +470,173 @@ tbbt_status tbbt_release_cache(void) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Entry point that allocates nothing (no counterpart in the paper).
+//
+// Some callers cannot allocate device memory when they call us: every byte
+// of the GPU may already belong to another allocator (a framework's caching
+// allocator that reserved the device), or the caller runs in a loop where
+// the host-device synchronisation implied by cudaMalloc/cudaFree is not
+// acceptable (the cost the paper avoids by pre-allocating outside the work
+// loop, Sec. 3.1), or it must never fail with out-of-memory at run time.
+// This variant runs the same kernels as the plan path but keeps all of their
+// scratch -- the sweep-major store, the stage-offset table, the per-unit
+// progress flags and the claim counter -- in one fixed array that exists
+// from the moment the library's device code is loaded.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;  // per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+struct NoAllocDevice {
+  int ready;
+  unsigned char *scratch;  // device address of g_noalloc_scratch on this device
+  int sms;
+};
+NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+std::mutex g_noalloc_mu;
+
+// Generation index of reflector (s, 0): the number of reflectors of stages
+// 0..s-1, sum over m = n-1-s .. n-2 of ceil(m / b), from the closed form
+// F(M) = sum_{m=1}^{M} ceil(m/b) = b q (q+1)/2 + r (q+1), M = q b + r.
+__global__ void fill_stage_offsets_kernel(int64_t *off, StoreGeom g) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s > (int64_t)g.n - 2) return;
+  auto F = [&](int64_t M) -> int64_t {
+    int64_t q = M / g.b, r = M - q * g.b;
+    return g.b * q * (q + 1) / 2 + r * (q + 1);
+  };
+  off[s] = F((int64_t)g.n - 2) - F((int64_t)g.n - 2 - s);
+}
+
+size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Per-device set-up, done by the first call on each device with that device
+// current: resolve the array's device address (the host-side name of a
+// __device__ array is only a stand-in) and allow the apply kernel the
+// largest dynamic shared memory any launch uses.
+tbbt_status noalloc_device(int *dev_out, NoAllocDevice **out) {
+  int dev = 0;
+  TBBT_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return TBBT_ENOTSUP;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  NoAllocDevice &d = g_noalloc_dev[dev];
+  if (!d.ready) {
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || ptr == nullptr) {
+      (void)cudaGetLastError();
+      return TBBT_ECUDA;
+    }
+    int sms = 0;
+    TBBT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    TBBT_CUDA_TRY(allow_max_dynamic_smem(tbbt::apply_kernel<double>));
+    TBBT_CUDA_TRY(allow_max_dynamic_smem(tbbt::apply_kernel<zdouble>));
+    d.scratch = (unsigned char *)ptr;
+    d.sms = sms;
+    d.ready = 1;
+  }
+  *dev_out = dev;
+  *out = &d;
+  return TBBT_OK;
+}
+
+template <typename T>
+tbbt_status noalloc_launch(NoAllocDevice &d, tbbt_dtype dtype, const void *hh_v, const void *hh_tau, int64_t n,
+                           int64_t nbw, int64_t nev, void *q, int64_t ldq, cudaStream_t s) {
+  const StoreGeom g{(int32_t)n, (int32_t)nbw, dtype == TBBT_COMPLEX128 ? 1 : 0};
+  const int64_t K = g.num_reflectors();
+  if (K == 0 || nev == 0) return TBBT_OK;
+  const size_t es = elem_size(dtype);
+  const int32_t ldv = round_even((int32_t)nbw);
+  // launch geometry: up to 8 sweeps per block and 8 stages per step, as
+  // many as fit in shared memory
+  int32_t G = 8, NB = 8;
+  while (smem_bytes_for(dtype, (int32_t)nbw, G, NB) > (size_t)kMaxSmem && (G > 1 || NB > 1)) {
+    if (G > 4 || (NB <= 2 && G > 1))
+      --G;
+    else
+      NB = NB > 1 ? NB / 2 : 1;
+  }
+  const size_t smem = smem_bytes_for(dtype, (int32_t)nbw, G, NB);
+  if (smem > (size_t)kMaxSmem) return TBBT_ENOTSUP;
+  const int32_t strips = (int32_t)((nev + 31) / 32);
+  const int32_t epochs = (g.num_sweeps() + G - 1) / G;
+  const int64_t units = (int64_t)strips * epochs;
+  // scratch layout: [store][stage offsets][flags][counter]
+  const size_t b_store = round256((size_t)K * ldv * es);
+  const size_t b_off = round256(sizeof(int64_t) * ((size_t)n + 1));
+  const size_t b_flags = round256(sizeof(int) * (size_t)units);
+  if (b_store + b_off + b_flags + sizeof(unsigned) > kNoAllocScratchBytes) return TBBT_ENOTSUP;
+  unsigned char *base = d.scratch;
+  T *store = reinterpret_cast<T *>(base);
+  int64_t *off = reinterpret_cast<int64_t *>(base + b_store);
+  int *flags = reinterpret_cast<int *>(base + b_store + b_off);
+  unsigned *counter = reinterpret_cast<unsigned *>(base + b_store + b_off + b_flags);
+
+  int per_sm = 0;
+  TBBT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tbbt::apply_kernel<T>, G * 32, smem));
+  if (per_sm < 1) return TBBT_ENOTSUP;
+
+  fill_stage_offsets_kernel<<<(unsigned)((n + 1 + 255) / 256), 256, 0, s>>>(off, g);
+  TBBT_CUDA_TRY(cudaGetLastError());
+  const int threads = 256;
+  const int64_t rblocks = (K + threads / 32 - 1) / (threads / 32);
+  tbbt::relayout_kernel<T><<<(unsigned)rblocks, threads, 0, s>>>((const T *)hh_v, (const T *)hh_tau, off, g, ldv,
+                                                                 store);
+  TBBT_CUDA_TRY(cudaGetLastError());
+  // the array keeps the previous call's contents: progress flags start at
+  // "nothing released" and the claim counter at zero on every call
+  TBBT_CUDA_TRY(cudaMemsetAsync(flags, 0x7f, sizeof(int) * (size_t)units, s));
+  TBBT_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned), s));
+  int *err = nullptr;
+  TBBT_CUDA_TRY(cudaGetSymbolAddress((void **)&err, g_tbbt_error));
+  tbbt::ApplyArgs a;
+  a.vstore = store;
+  a.q = q;
+  a.ldq = ldq;
+  a.g = g;
+  a.nev = (int32_t)nev;
+  a.ldv = ldv;
+  a.G = G;
+  a.NB = NB;
+  a.ring = ring_rows_for((int32_t)nbw, G, NB);
+  a.strips = strips;
+  a.units = (int32_t)units;
+  a.flags = flags;
+  a.counter = counter;
+  a.err = err;
+  a.timeout_ns = 20000000000LL;
+  a.withhold = -1;
+  const int64_t resident = (int64_t)d.sms * per_sm;
+  const unsigned grid = (unsigned)(units < resident ? units : resident);
+  tbbt::apply_kernel<T><<<grid, G * 32, smem, s>>>(a);
+  TBBT_CUDA_TRY(cudaGetLastError());
+  return TBBT_OK;
+}
+
+}  // namespace
+
+extern "C" tbbt_status tbbt_trans_ev_tridi_to_band_noalloc(tbbt_dtype dtype, const void *hh_v, const void *hh_tau,
+                                                           int64_t n, int64_t nbw, int64_t nev, void *q,
+                                                           int64_t ldq, void *stream) {
+  if (dtype != TBBT_REAL64 && dtype != TBBT_COMPLEX128) return TBBT_EINVAL;
+  tbbt_status st = check_shape(n, nbw, nev);
+  if (st != TBBT_OK) return st;
+  if (ldq < (n > 1 ? n : 1)) return TBBT_EINVAL;
+  const size_t es = elem_size(dtype);
+  const int64_t K = StoreGeom{(int32_t)n, (int32_t)nbw, dtype == TBBT_COMPLEX128 ? 1 : 0}.num_reflectors();
+  if (nev > 0 && (!q || (uintptr_t)q % es)) return TBBT_EINVAL;
+  if (nev > 0 && K > 0 && (!hh_v || !hh_tau || (uintptr_t)hh_v % es || (uintptr_t)hh_tau % es)) return TBBT_EINVAL;
+  if (nev == 0 || K == 0) return TBBT_OK;
+  int dev = 0;
+  NoAllocDevice *d = nullptr;
+  st = noalloc_device(&dev, &d);
+  if (st != TBBT_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dtype == TBBT_COMPLEX128) return noalloc_launch<zdouble>(*d, dtype, hh_v, hh_tau, n, nbw, nev, q, ldq, s);
+  return noalloc_launch<double>(*d, dtype, hh_v, hh_tau, n, nbw, nev, q, ldq, s);
+}
