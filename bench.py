@@ -55,8 +55,8 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "apply_kernel_traffic.json")
 
 def set_workload(name: str):
     global WORKLOAD
-    if name not in I.WORKLOADS or I.WORKLOADS[name]["complex_"]:
-        raise SystemExit(f"unknown or unsupported workload {name}")
+    if name not in I.WORKLOADS:
+        raise SystemExit(f"unknown workload {name}")
     WORKLOAD = name
 
 
@@ -176,7 +176,7 @@ def reference_arm(args, world, rank):
     w, v, tau, X, sum_l, flops_full = workload_inputs(WORKLOAD)
     ncols = args.ref_cols
     cols, Xs = cpu_sample(v, tau, X, w, ncols)
-    fl = 4 * len(cols) * sum_l
+    fl = (16 if w["complex_"] else 4) * len(cols) * sum_l
     for _ in range(args.warmup_ref):
         run_oracle_sample(v, tau, w, Xs)
     times, cores = [], 1
@@ -188,7 +188,7 @@ def reference_arm(args, world, rank):
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup_ref, "ms_per_step": 1e3 * total / len(times),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype_name(w), "data": "synthetic",
         "config": config_dict(w, "host cores; oracle sample"),
         "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
                          "sample": f"{len(cols)} of {w['nev']} columns, all {len(tau)} reflectors, per step"},
@@ -197,12 +197,21 @@ def reference_arm(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def esize(w):
+    return 16 if w["complex_"] else 8
+
+
+def dtype_name(w):
+    return "c128" if w["complex_"] else "f64"
+
+
 def config_dict(w, note=""):
-    return {"workload": WORKLOAD, "n": w["n"], "nbw": w["b"], "nev": w["nev"], "dtype": "real64",
+    return {"workload": WORKLOAD, "n": w["n"], "nbw": w["b"], "nev": w["nev"],
+            "dtype": "complex128" if w["complex_"] else "real64",
             "store": "seeded synthetic unitary reflectors, canonical store layout",
             "x": "seeded N(0,1/n) eigenvector block",
-            "l2": f"inputs larger than L2 (q {w['n'] * w['nev'] * 8 / 1e6:.0f} MB, store "
-                  f"{I.store_lengths(w['n'], w['b'], False).size * w['b'] * 8 / 1e6:.0f} MB)",
+            "l2": f"inputs larger than L2 (q {w['n'] * w['nev'] * esize(w) / 1e6:.0f} MB, store "
+                  f"{I.store_lengths(w['n'], w['b'], w['complex_']).size * w['b'] * esize(w) / 1e6:.0f} MB)",
             "parallelism": "replicas", "note": note}
 
 
@@ -249,12 +258,13 @@ def main():
     _native.load()  # the library must be built (fails loudly otherwise)
 
     w, v, tau, X, sum_l, flops = workload_inputs(WORKLOAD)
-    n, b, nev = w["n"], w["b"], w["nev"]
+    n, b, nev, cplx = w["n"], w["b"], w["nev"], w["complex_"]
+    es = esize(w)
     dv = torch.from_numpy(v).cuda()
     dt = torch.from_numpy(tau).cuda()
     q = torch.from_numpy(X.T.copy()).cuda().t()
     stream = torch.cuda.current_stream()
-    plan = P.Plan(False, n, b, nev)
+    plan = P.Plan(cplx, n, b, nev)
     info = plan.info()
 
     # parity pass on the pristine block (columns checked by the CPU baseline)
@@ -316,8 +326,9 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_s = float(tt.item())
     e2e = {"value": flops * args.e2e_steps * world / e2e_s / 1e12, "unit": "TFLOP/s",
-           "h2d_bytes_per_step": int(v.nbytes + tau.nbytes + n * nev * 8), "d2h_bytes_per_step": int(n * nev * 8),
-           "steps": args.e2e_steps, "api": "tbbt_trans_ev_tridi_to_band_host_d"}
+           "h2d_bytes_per_step": int(v.nbytes + tau.nbytes + n * nev * es), "d2h_bytes_per_step": int(n * nev * es),
+           "steps": args.e2e_steps,
+           "api": "tbbt_trans_ev_tridi_to_band_host_z" if cplx else "tbbt_trans_ev_tridi_to_band_host_d"}
 
     if rank == 0:
         apply_avg = sum(apply_ms) / len(apply_ms)
@@ -328,18 +339,19 @@ def main():
             peak_at_clock = SMS * DFMA_PER_CLK_SM * 2 * cs["sm_mhz"] * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": recorded_traffic(),
-                "kernel": "tbbt::apply_kernel<double>",
+                "kernel": "tbbt::apply_kernel<zdouble, 0>" if cplx else f"tbbt::apply_kernel<double, {b if b in (32, 64) else 0}>",
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe; DFMA probe 1.198 TF)",
                 "peak_at_sampled_clock": peak_at_clock,
-                "algorithmic_bytes_per_launch": int(2 * n * nev * 8 + sum_l * 8)}
+                "algorithmic_bytes_per_launch": int(2 * n * nev * es + sum_l * es)}
         Zo, cpu_s, cores = run_oracle_sample(v, tau, w, Xs)
-        cpu = {"value": 4 * len(cols) * sum_l / cpu_s / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+        cpu = {"value": (16 if cplx else 4) * len(cols) * sum_l / cpu_s / 1e12, "unit": "TFLOP/s", "cores": cores,
+               "kind": "oracle",
                "sample": f"{len(cols)} of {nev} columns, all {len(tau)} reflectors",
                "parity_max_abs_vs_gpu": float(np.abs(Zo - gpu_cols).max())}
         line = {
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(w),
+            "vs_baseline": None, "dtype": dtype_name(w), "data": "synthetic", "config": config_dict(w),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
             "clocks": cs, "relayout_ms_avg": sum(relayout_ms) / len(relayout_ms), "apply_ms_avg": apply_avg,
             "launch": info,

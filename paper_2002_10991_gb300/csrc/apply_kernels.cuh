@@ -132,6 +132,15 @@ __device__ __forceinline__ void cp_async(void *dst_smem, const void *src_gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Shared-memory load the compiler may not merge with other loads of the same
+// address (keeps reflector entries from being cached in registers across the
+// unrolled loops of the register-window variant, which would exhaust them).
+__device__ __forceinline__ double lds_f64(const double *p) {
+  double v;
+  asm volatile("ld.shared.f64 %0, [%1];\n" : "=d"(v) : "r"(smem_u32(p)));
+  return v;
+}
+
 // ---------------------------------------------------------------------------
 // the apply kernel
 // ---------------------------------------------------------------------------
@@ -320,8 +329,64 @@ __device__ __forceinline__ void apply_one(T *col, int32_t ring, int32_t r, int32
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(512, 1) apply_kernel(ApplyArgs a) {
+// Register-window variant of the stage loop for real data and b = B (32 or
+// 64): the lane keeps rows r .. r+B-1 of its column in registers, so neither
+// the dot-product chain nor the update touches shared memory. Per stage the
+// lane reads the one new top row from the ring, applies Eq. 8, and writes the
+// row that leaves the window at the bottom back to the ring (the next sweep
+// reads it there). The window moves up one row per stage; the move is folded
+// into the update, which runs from the bottom of the window up and writes
+// each updated element into the register of the element below it (just
+// consumed), so the window never needs a second copy. Rows >= n are held as
+// zeros and meet zero reflector entries (the store is zero-padded to
+// ldv = B), so they stay zero and are never written. Terms are summed and
+// updated exactly as in apply_one, so both variants give the same bits.
+template <int B>
+__device__ __forceinline__ void apply_stages_regwin(double (&x)[B], double *ring_col, int32_t ring, const StoreGeom &g,
+                                                    int32_t j, int32_t hi, int32_t lo, const double *vb,
+                                                    int32_t sig, int32_t ldv) {
+  const int32_t first = g.imax(j);
+  for (int32_t s = hi; s >= lo; --s) {
+    const int32_t r = g.row(s, j);
+    if (s == first) {
+      // first stage of the sweep: fill the whole window
+      int32_t sl = r % ring;
+#pragma unroll
+      for (int32_t t = 0; t < B; ++t) {
+        x[t] = (r + t < g.n) ? ring_col[(int64_t)sl * 32] : 0.0;
+        sl = (sl + 1 == ring) ? 0 : sl + 1;
+      }
+    } else {
+      x[0] = ring_col[(int64_t)(r % ring) * 32];  // rows r+1 .. r+B-1 are already in x[1..]
+    }
+    const double *ent = vb + (int64_t)(sig - s) * ldv;
+    double acc = x[0];
+#pragma unroll
+    for (int32_t t = 1; t < B; ++t) acc = fma(lds_f64(ent + t), x[t], acc);
+    const double u = lds_f64(ent) * acc;
+    if (s > 0) {
+      const double out = fma(-u, lds_f64(ent + B - 1), x[B - 1]);  // row r+B-1 leaves the window
+      if (r + B - 1 < g.n) ring_col[(int64_t)((r + B - 1) % ring) * 32] = out;
+#pragma unroll
+      for (int32_t t = B - 1; t > 1; --t) x[t] = fma(-u, lds_f64(ent + t - 1), x[t - 1]);
+      x[1] = x[0] - u;
+    } else {
+      // stage 0 ends the sweep: update in place; the whole window is final
+      x[0] -= u;
+#pragma unroll
+      for (int32_t t = 1; t < B; ++t) x[t] = fma(-u, lds_f64(ent + t), x[t]);
+      int32_t sl = r % ring;
+#pragma unroll
+      for (int32_t t = 0; t < B; ++t) {
+        if (r + t < g.n) ring_col[(int64_t)sl * 32] = x[t];
+        sl = (sl + 1 == ring) ? 0 : sl + 1;
+      }
+    }
+  }
+}
+
+template <typename T, int BW>
+__global__ void __launch_bounds__(BW > 0 ? 256 : 512, 1) apply_kernel(ApplyArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_unit;
   __shared__ int s_stop;
@@ -332,6 +397,8 @@ __global__ void __launch_bounds__(512, 1) apply_kernel(ApplyArgs a) {
   const StoreGeom &g = a.g;
   T *vbuf_w = vbuf + (int64_t)w * 2 * a.NB * a.ldv;
   T *mycol = ring + lane;
+  double xw[BW > 0 ? BW : 1];  // register window of the lane's column (BW > 0)
+  (void)xw;
 
   for (;;) {
     if (threadIdx.x == 0) {
@@ -385,8 +452,12 @@ __global__ void __launch_bounds__(512, 1) apply_kernel(ApplyArgs a) {
           const int32_t j = ep.j0 + w;
           const int32_t sig = ep.sig_top - (t - w) * ep.nb;
           const T *vb = vbuf_w + (int64_t)(t & 1) * ep.nb * a.ldv;
-          for (int32_t s = hi; s >= lo; --s)
-            apply_one<T>(mycol, a.ring, g.row(s, j), g.len(s, j), vb + (int64_t)(sig - s) * a.ldv);
+          if constexpr (BW > 0) {
+            apply_stages_regwin<BW>(xw, mycol, a.ring, g, j, hi, lo, vb, sig, a.ldv);
+          } else {
+            for (int32_t s = hi; s >= lo; --s)
+              apply_one<T>(mycol, a.ring, g.row(s, j), g.len(s, j), vb + (int64_t)(sig - s) * a.ldv);
+          }
         }
         pf.commit(a, ring, ntop, top);
         top = ntop;

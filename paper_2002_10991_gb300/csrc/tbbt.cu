@@ -57,6 +57,16 @@ cudaError_t allow_max_dynamic_smem(K kernel) {
 
 size_t elem_size(tbbt_dtype dt) { return dt == TBBT_COMPLEX128 ? 16 : 8; }
 
+using ApplyFn = void (*)(tbbt::ApplyArgs);
+
+// The apply kernel instance for a data type and register-window width.
+ApplyFn apply_fn(tbbt_dtype dt, int32_t bw) {
+  if (dt == TBBT_COMPLEX128) return tbbt::apply_kernel<zdouble, 0>;
+  if (bw == 64) return tbbt::apply_kernel<double, 64>;
+  if (bw == 32) return tbbt::apply_kernel<double, 32>;
+  return tbbt::apply_kernel<double, 0>;
+}
+
 int32_t ring_rows_for(int32_t b, int32_t G, int32_t NB) { return G * b + (G + 2) * NB + 8; }
 
 size_t smem_bytes_for(tbbt_dtype dt, int32_t b, int32_t G, int32_t NB) {
@@ -80,6 +90,7 @@ struct tbbt_plan {
   int64_t K;
   int32_t ldv;
   int32_t G, NB, ring;
+  int32_t bw;  // register-window width of the apply kernel (0: shared-memory window)
   size_t smem;
   void *d_store = nullptr;       // re-laid reflectors, K * ldv elements
   int64_t *d_stage_off = nullptr;  // n entries
@@ -180,8 +191,15 @@ tbbt_status tbbt_plan_create(tbbt_plan **plan, tbbt_dtype dtype, int64_t n, int6
   p->nev = (int32_t)nev;
   p->K = p->g.num_reflectors();
   p->ldv = round_even((int32_t)nbw);
+  // real data with b = 32 or 64 keep each column's window in registers
+  p->bw = (dtype == TBBT_REAL64 && (nbw == 32 || nbw == 64)) ? (int32_t)nbw : 0;
   // launch geometry: most sweeps per block that fit in shared memory
-  int32_t wantG = opt && opt->sweeps_per_block > 0 ? opt->sweeps_per_block : 8;
+  // Default: 4 sweeps per block (one warp per SM sub-partition) and 8 stages
+  // per step; two such blocks share an SM when they fit, so one block's
+  // pipeline fill is covered by the other. Block widths that are not a
+  // multiple of 4 load the sub-partitions unevenly and are slower.
+  int32_t wantG = opt && opt->sweeps_per_block > 0 ? opt->sweeps_per_block : 4;
+  if (p->bw > 0 && wantG > 8) wantG = 8;  // 256 threads: room for the register window
   int32_t wantNB = opt && opt->stages_per_step > 0 ? opt->stages_per_step : 8;
   if (wantG > 16) wantG = 16;
   int32_t G = wantG, NB = wantNB;
@@ -239,10 +257,7 @@ tbbt_status tbbt_plan_create(tbbt_plan **plan, tbbt_dtype dtype, int64_t n, int6
   // The attribute belongs to the kernel, not to the plan: raise it to the
   // largest size any plan may use, so that creating a plan with a smaller
   // footprint never invalidates the launches of an earlier, larger one.
-  if (dtype == TBBT_COMPLEX128)
-    e = allow_max_dynamic_smem(tbbt::apply_kernel<zdouble>);
-  else
-    e = allow_max_dynamic_smem(tbbt::apply_kernel<double>);
+  e = allow_max_dynamic_smem(apply_fn(dtype, p->bw));
   if (e != cudaSuccess) return fail(TBBT_ECUDA);
   if (p->units > 0) {
     e = cudaMalloc(&p->d_flags, sizeof(int) * (size_t)p->units);
@@ -255,10 +270,7 @@ tbbt_status tbbt_plan_create(tbbt_plan **plan, tbbt_dtype dtype, int64_t n, int6
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return fail(TBBT_ECUDA);
-    if (dtype == TBBT_COMPLEX128)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tbbt::apply_kernel<zdouble>, G * 32, p->smem);
-    else
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tbbt::apply_kernel<double>, G * 32, p->smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_fn(dtype, p->bw), G * 32, p->smem);
     if (e != cudaSuccess || per_sm < 1) return fail(TBBT_ECUDA);
     int64_t resident = (int64_t)sms * per_sm;
     p->grid = (int32_t)(p->units < resident ? p->units : resident);
@@ -326,10 +338,7 @@ tbbt_status tbbt_plan_execute(tbbt_plan *p, void *q, int64_t ldq, void *stream) 
   TBBT_CUDA_TRY(cudaMemsetAsync(p->d_flags, 0x7f, sizeof(int) * (size_t)p->units, s));
   TBBT_CUDA_TRY(cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned), s));
   unsigned blocks = (unsigned)p->grid;
-  if (p->dtype == TBBT_COMPLEX128)
-    tbbt::apply_kernel<zdouble><<<blocks, p->G * 32, p->smem, s>>>(a);
-  else
-    tbbt::apply_kernel<double><<<blocks, p->G * 32, p->smem, s>>>(a);
+  apply_fn(p->dtype, p->bw)<<<blocks, p->G * 32, p->smem, s>>>(a);
   TBBT_CUDA_TRY(cudaGetLastError());
   return TBBT_OK;
 }
@@ -533,8 +542,8 @@ tbbt_status noalloc_device(int *dev_out, NoAllocDevice **out) {
     }
     int sms = 0;
     TBBT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    TBBT_CUDA_TRY(allow_max_dynamic_smem(tbbt::apply_kernel<double>));
-    TBBT_CUDA_TRY(allow_max_dynamic_smem(tbbt::apply_kernel<zdouble>));
+    TBBT_CUDA_TRY(allow_max_dynamic_smem(tbbt::apply_kernel<double, 0>));
+    TBBT_CUDA_TRY(allow_max_dynamic_smem(tbbt::apply_kernel<zdouble, 0>));
     d.scratch = (unsigned char *)ptr;
     d.sms = sms;
     d.ready = 1;
@@ -578,7 +587,7 @@ tbbt_status noalloc_launch(NoAllocDevice &d, tbbt_dtype dtype, const void *hh_v,
   unsigned *counter = reinterpret_cast<unsigned *>(base + b_store + b_off + b_flags);
 
   int per_sm = 0;
-  TBBT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tbbt::apply_kernel<T>, G * 32, smem));
+  TBBT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tbbt::apply_kernel<T, 0>, G * 32, smem));
   if (per_sm < 1) return TBBT_ENOTSUP;
 
   fill_stage_offsets_kernel<<<(unsigned)((n + 1 + 255) / 256), 256, 0, s>>>(off, g);
@@ -613,7 +622,7 @@ tbbt_status noalloc_launch(NoAllocDevice &d, tbbt_dtype dtype, const void *hh_v,
   a.withhold = -1;
   const int64_t resident = (int64_t)d.sms * per_sm;
   const unsigned grid = (unsigned)(units < resident ? units : resident);
-  tbbt::apply_kernel<T><<<grid, G * 32, smem, s>>>(a);
+  tbbt::apply_kernel<T, 0><<<grid, G * 32, smem, s>>>(a);
   TBBT_CUDA_TRY(cudaGetLastError());
   return TBBT_OK;
 }

@@ -208,6 +208,7 @@ WORKLOADS = {
     "real-n32768-b64-dft": dict(n=32768, b=64, nev=9830, complex_=False, kind="dft", seed=SEED_BASE + 4),
     # a smaller case of the same kernel for profiler captures (q still larger than L2)
     "real-n4096-b64-dft": dict(n=4096, b=64, nev=4096, complex_=False, kind="dft", seed=SEED_BASE + 6),
+    "complex-n4096-b64-dft": dict(n=4096, b=64, nev=2048, complex_=True, kind="dft", seed=SEED_BASE + 7),
 }
 
 

@@ -137,6 +137,21 @@ def test_launch_geometry_does_not_change_bits(P, cplx):
     assert maxdiff(outs[0], Zo) <= TOL
 
 
+@pytest.mark.parametrize("b", [32, 64])
+def test_register_window_matches_shared_window_bitwise(P, b):
+    # real b = 32 / 64 plans keep each column's window in registers; the
+    # allocation-free entry point runs the shared-memory window kernel. Both
+    # apply the same operations in the same order.
+    n, nev = 1500, 200
+    v, tau = I.synthetic_store(n, b, 40 + b, False)
+    X = I.eigvec_block(n, nev, 41 + b, False)
+    reg = gpu_apply(P, v, tau, n, b, X)
+    q = torch.from_numpy(X.T.copy()).cuda().t()
+    P.trans_ev_tridi_to_band_noalloc(dev(v), dev(tau), n, b, nev, q)
+    P.stream_check()
+    assert np.array_equal(reg, q.cpu().numpy())
+
+
 def test_repeat_runs_bitwise_identical(P):
     n, b, nev = 1000, 64, 200
     v, tau = I.synthetic_store(n, b, 11, False)
