@@ -53,11 +53,83 @@ FP64_PEAK_TFLOPS = SMS * DFMA_PER_CLK_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "apply_kernel_traffic.json")
 
 
+BATCH_WORKLOAD = "batch-64-mixed"
+
+
 def set_workload(name: str):
     global WORKLOAD
-    if name not in I.WORKLOADS:
+    if name not in I.WORKLOADS and name != BATCH_WORKLOAD:
         raise SystemExit(f"unknown workload {name}")
     WORKLOAD = name
+
+
+def batch_bench(args):
+    """The batched form: 64 problems (N uniform in [1000, 6000], nev = N/2,
+    b = 32, even p real, odd p complex) in one persistent graph-replayed
+    launch, against the same problems as 64 sequential plan launches."""
+    import torch
+
+    import paper_2002_10991_gb300 as P
+
+    torch.cuda.set_device(0)
+    specs = I.batch_workload()
+    probs, flops = [], 0
+    for s in specs:
+        n, b, nev, c = s["n"], s["b"], s["nev"], s["complex_"]
+        v, tau = I.synthetic_store(n, b, s["seed"], c)
+        X = I.eigvec_block(n, nev, s["seed"] + 1, c)
+        probs.append((torch.from_numpy(v).cuda(), torch.from_numpy(tau).cuda(), n, b, nev,
+                      torch.from_numpy(X.T.copy()).cuda().t()))
+        flops += (16 if c else 4) * nev * int(I.store_lengths(n, b, c).sum())
+    t0 = time.perf_counter()
+    batch = P.Batch(probs, autotune=args.autotune, autotune_cache=os.environ.get("TBBT_AUTOTUNE_CACHE"))
+    create_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    batch.execute()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clocks:
+        e0.record(stream)
+        for _ in range(args.steps):
+            batch.execute()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    P.stream_check()
+    batched_ms = e0.elapsed_time(e1) / args.steps
+    # the same problems, one plain plan launch after another
+    plans = [P.Plan(bool(s["complex_"]), s["n"], s["b"], s["nev"]) for s in specs]
+    for pl, (dv, dt, n, b, nev, q) in zip(plans, probs):
+        pl.set_reflectors(dv, dt)
+        pl.execute(q)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        for pl, (dv, dt, n, b, nev, q) in zip(plans, probs):
+            pl.set_reflectors(dv, dt)
+            pl.execute(q)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    P.stream_check()
+    seq_ms = e0.elapsed_time(e1) / args.steps
+    value = flops / (batched_ms * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": 1,
+        "ms_per_step": batched_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64+c128", "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD, "problems": len(specs), "n_range": [min(s["n"] for s in specs),
+                   max(s["n"] for s in specs)], "nbw": 32, "nev": "n/2", "complex_problems": sum(s["complex_"] for s in specs),
+                   "store": "seeded synthetic unitary reflectors", "flops_per_step": flops},
+        "batched": {"ms": batched_ms, "tflops": value, "launch": batch.info(), "create_s": create_s},
+        "sequential": {"ms": seq_ms, "tflops": flops / (seq_ms * 1e-3) / 1e12, "launches_per_step": 2 * len(specs)},
+        "speedup_vs_sequential": seq_ms / batched_ms,
+        "roofline": {"bound": "alu", "achieved": value, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": value / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "tbbt::batch_kernel"},
+        "clocks": clocks.summary(), "gpu_launches": 1 + len(specs),
+    }
+    print(json.dumps(line), flush=True)
+    batch.close()
+    for pl in plans:
+        pl.close()
 
 
 def csrc_hash() -> str:
@@ -226,9 +298,14 @@ def main():
     ap.add_argument("--warmup-ref", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--workload", default=WORKLOAD,
-                    help="named workload (default: the benchmark workload; others are for profiler captures)")
+                    help="named workload (default: the benchmark workload; others are for profiler captures "
+                         "and the batched-form measurement)")
+    ap.add_argument("--autotune", action="store_true", help="batched workload: tune the launch geometry first")
     args = ap.parse_args()
     set_workload(args.workload)
+    if WORKLOAD == BATCH_WORKLOAD:
+        batch_bench(args)
+        return
     world, rank, local = dist_setup()
 
     if args.impl == "reference":

@@ -156,6 +156,56 @@ tbbt_status tbbt_plan_destroy(tbbt_plan *plan);
 tbbt_status tbbt_plan_info(const tbbt_plan *plan, int32_t *sweeps_per_block, int32_t *stages_per_step,
                            int32_t *ring_rows, int32_t *smem_bytes, int32_t *blocks);
 
+/* ---------------------------------------------------------------------------
+ * Batched form: many independent problems of uneven size (for example the
+ * k-points and spin channels of one KS-DFT iteration, Sec. 5), real and
+ * complex mixed, back-transformed by ONE persistent kernel launch. All
+ * pointers are device pointers fixed at creation: the batch captures a CUDA
+ * graph (re-layout of every store, queue reset, the persistent launch), and
+ * each execute replays it on the caller's stream, reading the stores and
+ * updating every q in place. Update the contents of the arrays between
+ * executes, not their addresses.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  tbbt_dtype dtype;  /* TBBT_REAL64 or TBBT_COMPLEX128 */
+  int32_t reserved0;
+  int64_t n, nbw, nev; /* as for the one-shot calls */
+  const void *hh_v;    /* canonical store, device */
+  const void *hh_tau;
+  void *q; /* n x nev, column-major, device, updated in place */
+  int64_t ldq;
+} tbbt_problem;
+
+typedef struct tbbt_batch tbbt_batch;
+
+typedef struct {
+  int32_t sweeps_per_block;        /* 0 = 4 (4 or 8) */
+  int32_t stages_per_step_real;    /* 0 = 16 */
+  int32_t stages_per_step_complex; /* 0 = 4; defaults are lowered until two blocks fit an SM */
+  /* Nonzero: time candidate geometries at creation on scratch copies of
+   * every q (the caller's data are not touched) and keep the fastest. Results
+   * are cached per process and GPU and, if autotune_cache (or the environment
+   * variable TBBT_AUTOTUNE_CACHE) names a file, appended to it and read back
+   * by later processes. Tuning runs the whole batch several times. */
+  int32_t autotune;
+  const char *autotune_cache;
+  int32_t wait_timeout_ms; /* 0 = 20000, see tbbt_options */
+  int32_t reserved[5];
+} tbbt_batch_options;
+
+/* Creates a batch of `count` problems (opt may be NULL). Allocates all
+ * workspace and instantiates the graph; synchronises. */
+tbbt_status tbbt_batch_create(tbbt_batch **batch, int32_t count, const tbbt_problem *problems,
+                              const tbbt_batch_options *opt);
+/* Enqueues one replay of the batch's graph on `stream`. */
+tbbt_status tbbt_batch_execute(tbbt_batch *batch, void *stream);
+/* Geometry in use: sweeps per block, stages per step (real / complex),
+ * persistent blocks, queued work units, whether it came from tuning. */
+tbbt_status tbbt_batch_info(const tbbt_batch *batch, int32_t *sweeps_per_block, int32_t *stages_real,
+                            int32_t *stages_complex, int32_t *blocks, int64_t *units, int32_t *tuned);
+/* Destroys a batch (synchronises the device). Accepts NULL. */
+tbbt_status tbbt_batch_destroy(tbbt_batch *batch);
+
 /* Synchronises `stream`, then reports (and clears) the device error word:
  * TBBT_OK, TBBT_ETIMEOUT, or TBBT_ECUDA if the stream itself failed. The
  * word is sticky: after a timeout, later launches return at once without

@@ -3,6 +3,7 @@
 and this thin Python binding."""
 
 from .api import (  # noqa: F401
+    Batch,
     Plan,
     TbbtError,
     num_reflectors,

@@ -83,6 +83,15 @@ def load():
         L.tbbt_stream_check.argtypes = [p]
         L.tbbt_trans_ev_tridi_to_band_noalloc.restype = c_int
         L.tbbt_trans_ev_tridi_to_band_noalloc.argtypes = [c_int, p, p, i64, i64, i64, p, i64, p]
+        L.tbbt_batch_create.restype = c_int
+        L.tbbt_batch_create.argtypes = [ctypes.POINTER(p), i32, p, p]
+        L.tbbt_batch_execute.restype = c_int
+        L.tbbt_batch_execute.argtypes = [p, p]
+        L.tbbt_batch_info.restype = c_int
+        L.tbbt_batch_info.argtypes = [p, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                      ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32)]
+        L.tbbt_batch_destroy.restype = c_int
+        L.tbbt_batch_destroy.argtypes = [p]
         L.tbbt_schedule_max_live_rows.restype = i64
         L.tbbt_schedule_max_live_rows.argtypes = [i64, i64, c_int, i32, i32]
         _lib = L

@@ -189,3 +189,69 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class Problem(ctypes.Structure):
+    """tbbt_problem: one problem of a batch (device pointers)."""
+    _fields_ = [("dtype", ctypes.c_int), ("reserved0", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("nbw", ctypes.c_int64), ("nev", ctypes.c_int64), ("hh_v", ctypes.c_void_p),
+                ("hh_tau", ctypes.c_void_p), ("q", ctypes.c_void_p), ("ldq", ctypes.c_int64)]
+
+
+class BatchOptions(ctypes.Structure):
+    _fields_ = [("sweeps_per_block", ctypes.c_int32), ("stages_per_step_real", ctypes.c_int32),
+                ("stages_per_step_complex", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("autotune_cache", ctypes.c_char_p), ("wait_timeout_ms", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
+
+
+class Batch:
+    """tbbt_batch: many problems back-transformed by one persistent launch,
+    replayed from a CUDA graph. ``problems`` is a list of
+    ``(hh_v, hh_tau, n, nbw, nev, q)`` with CUDA tensors (q column-major);
+    the tensors must stay alive and at the same addresses while the batch is
+    used (the batch keeps references)."""
+
+    def __init__(self, problems, sweeps_per_block: int = 0, stages_per_step_real: int = 0,
+                 stages_per_step_complex: int = 0, autotune: bool = False, autotune_cache: str | None = None,
+                 wait_timeout_ms: int = 0):
+        self._keep = []
+        arr = (Problem * len(problems))()
+        for i, (hh_v, hh_tau, n, nbw, nev, q) in enumerate(problems):
+            cplx = _is_complex_dtype(q)
+            ldq, _ = _q_layout(q, n)
+            arr[i] = Problem(COMPLEX128 if cplx else REAL64, 0, n, nbw, nev,
+                             hh_v.data_ptr() if hh_v.numel() else None,
+                             hh_tau.data_ptr() if hh_tau.numel() else None,
+                             q.data_ptr() if q.numel() else None, ldq)
+            self._keep += [hh_v, hh_tau, q]
+        self._cache = autotune_cache.encode() if autotune_cache else None
+        opt = BatchOptions(sweeps_per_block, stages_per_step_real, stages_per_step_complex, int(autotune),
+                           self._cache, wait_timeout_ms)
+        self._h = ctypes.c_void_p()
+        st = _native.load().tbbt_batch_create(ctypes.byref(self._h), len(problems), ctypes.cast(arr, ctypes.c_void_p),
+                                              ctypes.byref(opt))
+        _check(st, "tbbt_batch_create")
+
+    def execute(self, stream=None):
+        _check(_native.load().tbbt_batch_execute(self._h, _stream_handle(stream)), "tbbt_batch_execute")
+
+    def info(self):
+        i32 = [ctypes.c_int32() for _ in range(4)]
+        units = ctypes.c_int64()
+        tuned = ctypes.c_int32()
+        _check(_native.load().tbbt_batch_info(self._h, *[ctypes.byref(v) for v in i32], ctypes.byref(units),
+                                              ctypes.byref(tuned)), "tbbt_batch_info")
+        return {"sweeps_per_block": i32[0].value, "stages_real": i32[1].value, "stages_complex": i32[2].value,
+                "blocks": i32[3].value, "units": units.value, "tuned": bool(tuned.value)}
+
+    def close(self):
+        if self._h:
+            _native.load().tbbt_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -385,11 +385,15 @@ __device__ __forceinline__ void apply_stages_regwin(double (&x)[B], double *ring
   }
 }
 
+// One work unit: strip c0 .. c0+31 of the problem described by `a`, epoch e
+// (sweeps e*G .. e*G+G-1). `myflag` receives this unit's progress, `prevflag`
+// is the previous epoch's of the same strip (null for epoch 0). `s_stop` is a
+// shared word used to broadcast waits that gave up. Returns false if the
+// unit was abandoned.
 template <typename T, int BW>
-__global__ void __launch_bounds__(BW > 0 ? 256 : 512, 1) apply_kernel(ApplyArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_unit;
-  __shared__ int s_stop;
+__device__ __forceinline__ bool process_unit(const ApplyArgs &a, int32_t e, int32_t c0, int *myflag,
+                                             const int *prevflag, bool publish, unsigned char *smem_raw,
+                                             int *s_stop) {
   T *ring = reinterpret_cast<T *>(smem_raw);
   T *vbuf = ring + (int64_t)a.ring * 32;
   const int lane = threadIdx.x & 31;
@@ -399,7 +403,77 @@ __global__ void __launch_bounds__(BW > 0 ? 256 : 512, 1) apply_kernel(ApplyArgs 
   T *mycol = ring + lane;
   double xw[BW > 0 ? BW : 1];  // register window of the lane's column (BW > 0)
   (void)xw;
+  const Epoch ep = make_epoch(g, e, a.G, a.NB);
 
+  // prologue: rows needed at step 0 and the reflectors of step 0
+  int32_t top = step_min_row(g, ep, 0);
+  if (threadIdx.x == 0) *s_stop = prevflag ? wait_released(a, prevflag, top) : 0;
+  __syncthreads();
+  bool abandoned = *s_stop != 0;
+  if (!abandoned) {
+    load_rows_now<T>(a, ring, top, g.n, c0);
+    load_reflectors<T>(a, ep, vbuf_w, w, 0, lane);
+    cp_async_wait_all();
+    __syncthreads();
+    int32_t released = g.n;  // rows >= released are back in global memory
+    RowPrefetch<T> pf;
+    for (int32_t t = 0; t < ep.nsteps; ++t) {
+      // rows no warp touches from step t on go back to global memory
+      int32_t live = rows_live_max(g, ep, t);
+      int32_t rel = live + 1 > top ? live + 1 : top;
+      if (rel < released) {
+        store_rows<T>(a, ring, rel, released, c0);
+        released = rel;
+      }
+      // rows of step t+1 must have been released by the previous epoch
+      const int32_t ntop = step_min_row(g, ep, t + 1);
+      if (threadIdx.x == 0) *s_stop = (prevflag && ntop < top) ? wait_released(a, prevflag, ntop) : 0;
+      __syncthreads();
+      if (*s_stop) {
+        abandoned = true;
+        break;
+      }
+      if (threadIdx.x == 0 && publish) st_release(myflag, released);
+      pf.issue(a, ntop, top, c0);
+      load_reflectors<T>(a, ep, vbuf_w, w, t + 1, lane);
+      // this warp's stages of step t
+      int32_t hi, lo;
+      warp_stages(g, ep, w, t, &hi, &lo);
+      if (hi >= lo) {
+        const int32_t j = ep.j0 + w;
+        const int32_t sig = ep.sig_top - (t - w) * ep.nb;
+        const T *vb = vbuf_w + (int64_t)(t & 1) * ep.nb * a.ldv;
+        if constexpr (BW > 0) {
+          apply_stages_regwin<BW>(xw, mycol, a.ring, g, j, hi, lo, vb, sig, a.ldv);
+        } else {
+          for (int32_t s = hi; s >= lo; --s)
+            apply_one<T>(mycol, a.ring, g.row(s, j), g.len(s, j), vb + (int64_t)(sig - s) * a.ldv);
+        }
+      }
+      pf.commit(a, ring, ntop, top);
+      top = ntop;
+      cp_async_wait_all();
+      __syncthreads();
+    }
+    if (!abandoned) {
+      // the rest of the strip is final for this epoch
+      store_rows<T>(a, ring, top, released, c0);
+      __syncthreads();
+      if (threadIdx.x == 0 && publish) st_release(myflag, top);
+    }
+  }
+  if (abandoned) {
+    cp_async_wait_all();
+    if (threadIdx.x == 0) st_release(myflag, kPoison);
+  }
+  return !abandoned;
+}
+
+template <typename T, int BW>
+__global__ void __launch_bounds__(BW > 0 ? 256 : 512, 1) apply_kernel(ApplyArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_unit;
+  __shared__ int s_stop;
   for (;;) {
     if (threadIdx.x == 0) {
       s_unit = (int)atomicAdd(a.counter, 1u);
@@ -410,71 +484,79 @@ __global__ void __launch_bounds__(BW > 0 ? 256 : 512, 1) apply_kernel(ApplyArgs 
     if (u >= a.units || s_stop) break;
     const int32_t e = u / a.strips;
     const int32_t c0 = (u - e * a.strips) * 32;
-    int *myflag = a.flags + u;
-    const int *prevflag = e > 0 ? a.flags + (u - a.strips) : nullptr;
-    const Epoch ep = make_epoch(g, e, a.G, a.NB);
-
-    // prologue: rows needed at step 0 and the reflectors of step 0
-    int32_t top = step_min_row(g, ep, 0);
-    if (threadIdx.x == 0) s_stop = prevflag ? wait_released(a, prevflag, top) : 0;
+    process_unit<T, BW>(a, e, c0, a.flags + u, e > 0 ? a.flags + (u - a.strips) : nullptr, u != a.withhold,
+                        smem_raw, &s_stop);
     __syncthreads();
-    bool abandoned = s_stop != 0;
-    if (!abandoned) {
-      load_rows_now<T>(a, ring, top, g.n, c0);
-      load_reflectors<T>(a, ep, vbuf_w, w, 0, lane);
-      cp_async_wait_all();
-      __syncthreads();
-      int32_t released = g.n;  // rows >= released are back in global memory
-      RowPrefetch<T> pf;
-      for (int32_t t = 0; t < ep.nsteps; ++t) {
-        // rows no warp touches from step t on go back to global memory
-        int32_t live = rows_live_max(g, ep, t);
-        int32_t rel = live + 1 > top ? live + 1 : top;
-        if (rel < released) {
-          store_rows<T>(a, ring, rel, released, c0);
-          released = rel;
-        }
-        // rows of step t+1 must have been released by the previous epoch
-        const int32_t ntop = step_min_row(g, ep, t + 1);
-        if (threadIdx.x == 0) s_stop = (prevflag && ntop < top) ? wait_released(a, prevflag, ntop) : 0;
-        __syncthreads();
-        if (s_stop) {
-          abandoned = true;
-          break;
-        }
-        if (threadIdx.x == 0 && u != a.withhold) st_release(myflag, released);
-        pf.issue(a, ntop, top, c0);
-        load_reflectors<T>(a, ep, vbuf_w, w, t + 1, lane);
-        // this warp's stages of step t
-        int32_t hi, lo;
-        warp_stages(g, ep, w, t, &hi, &lo);
-        if (hi >= lo) {
-          const int32_t j = ep.j0 + w;
-          const int32_t sig = ep.sig_top - (t - w) * ep.nb;
-          const T *vb = vbuf_w + (int64_t)(t & 1) * ep.nb * a.ldv;
-          if constexpr (BW > 0) {
-            apply_stages_regwin<BW>(xw, mycol, a.ring, g, j, hi, lo, vb, sig, a.ldv);
-          } else {
-            for (int32_t s = hi; s >= lo; --s)
-              apply_one<T>(mycol, a.ring, g.row(s, j), g.len(s, j), vb + (int64_t)(sig - s) * a.ldv);
-          }
-        }
-        pf.commit(a, ring, ntop, top);
-        top = ntop;
-        cp_async_wait_all();
-        __syncthreads();
-      }
-      if (!abandoned) {
-        // the rest of the strip is final for this epoch
-        store_rows<T>(a, ring, top, released, c0);
-        __syncthreads();
-        if (threadIdx.x == 0 && u != a.withhold) st_release(myflag, top);
-      }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// batched form: many problems, one persistent launch
+// ---------------------------------------------------------------------------
+// Every problem keeps its own ApplyArgs (geometry, store, q, step length,
+// ring size); the units of all problems form one queue whose order keeps
+// every dependency pointing to an earlier unit (epoch-major across problems,
+// longest problems first within an epoch), so the same no-deadlock argument
+// holds. A block copies the arguments of its unit's problem into shared
+// memory and dispatches on the problem's kind.
+enum BatchKind : int32_t { kRealGeneric = 0, kReal32 = 1, kComplex = 3 };
+
+struct BatchProblem {
+  ApplyArgs a;  // flags/counter/err/units/strips fields unused here
+  int32_t kind;
+  int32_t pad;
+};
+
+struct BatchUnit {
+  int32_t problem, strip, epoch, prev;  // prev: queue index of (problem, strip, epoch-1), or -1
+};
+
+struct BatchArgs {
+  const BatchProblem *problems;
+  const BatchUnit *units;
+  int32_t nunits;
+  int *flags;  // one per queue entry
+  unsigned *counter;
+  int *err;
+};
+
+__global__ void __launch_bounds__(256, 1) batch_kernel(BatchArgs b) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_unit;
+  __shared__ int s_stop;
+  __shared__ BatchProblem s_prob;
+  __shared__ BatchUnit s_u;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_unit = (int)atomicAdd(b.counter, 1u);
+      s_stop = (*(volatile int *)b.err != 0);
     }
-    if (abandoned) {
-      cp_async_wait_all();
-      if (threadIdx.x == 0) st_release(myflag, kPoison);
+    __syncthreads();
+    const int u = s_unit;
+    if (u >= b.nunits || s_stop) break;
+    // stage this unit's problem arguments in shared memory (word copy)
+    {
+      const int *src = reinterpret_cast<const int *>(b.problems + b.units[u].problem);
+      int *dst = reinterpret_cast<int *>(&s_prob);
+      for (int i = threadIdx.x; i < (int)(sizeof(BatchProblem) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+      if (threadIdx.x == 0) s_u = b.units[u];
     }
+    __syncthreads();
+    ApplyArgs a = s_prob.a;
+    a.err = b.err;
+    const int kind = s_prob.kind;
+    const BatchUnit un = s_u;
+    int *myflag = b.flags + u;
+    const int *prevflag = un.prev >= 0 ? b.flags + un.prev : nullptr;
+    const int32_t c0 = un.strip * 32;
+    // (b = 64 real problems take the shared-memory window here: the 64-row
+    // register window would not fit beside the other paths of this kernel)
+    if (kind == kReal32)
+      process_unit<double, 32>(a, un.epoch, c0, myflag, prevflag, true, smem_raw, &s_stop);
+    else if (kind == kComplex)
+      process_unit<zdouble, 0>(a, un.epoch, c0, myflag, prevflag, true, smem_raw, &s_stop);
+    else
+      process_unit<double, 0>(a, un.epoch, c0, myflag, prevflag, true, smem_raw, &s_stop);
     __syncthreads();
   }
 }

@@ -40,6 +40,8 @@ __device__ int g_tbbt_error = 0;
 
 int32_t round_even(int32_t b) { return (b + 1) & ~1; }
 
+size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
+
 // Raise the kernel's dynamic shared memory limit to what the device allows
 // beside its static shared memory (at least kMaxSmem on sm_103).
 template <typename K>
@@ -480,6 +482,8 @@ tbbt_status tbbt_release_cache(void) {
 
 }  // extern "C"
 
+#include "batch.cuh"
+
 // ---------------------------------------------------------------------------
 // Entry point that allocates nothing (no counterpart in the paper).
 //
@@ -520,8 +524,6 @@ __global__ void fill_stage_offsets_kernel(int64_t *off, StoreGeom g) {
   };
   off[s] = F((int64_t)g.n - 2) - F((int64_t)g.n - 2 - s);
 }
-
-size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Per-device set-up, done by the first call on each device with that device
 // current: resolve the array's device address (the host-side name of a

@@ -223,3 +223,12 @@ def batch_sizes(count: int = 64, seed: int = SEED_BASE + 5, lo: int = 1000, hi: 
     """Problem sizes of the batched workload: N_p = lo + floor(u*(hi-lo+1))."""
     u = uniform(seed, 31, (count,))
     return (lo + np.floor(u * (hi - lo + 1))).astype(np.int64)
+
+
+def batch_workload(count: int = 64, seed: int = SEED_BASE + 5, b: int = 32):
+    """The batched workload: ``count`` problems with N_p drawn from
+    ``batch_sizes``, even p real and odd p complex, semi-bandwidth ``b``,
+    nev = floor(N_p / 2). Returns a list of dicts (n, b, nev, complex_, seed)."""
+    sizes = batch_sizes(count, seed)
+    return [dict(n=int(n), b=b, nev=int(n) // 2, complex_=bool(p % 2), seed=seed * 131 + p)
+            for p, n in enumerate(sizes)]

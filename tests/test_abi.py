@@ -105,3 +105,22 @@ def test_generator_is_deterministic_and_counter_based():
     nrm2 = np.sum(np.abs(V) ** 2, axis=1)
     # unitary: 2 Re(tau) = |tau|^2 |v|^2
     assert np.abs(2 * tau.real - np.abs(tau) ** 2 * nrm2).max() < 1e-13
+
+
+def test_batch_argument_checks_fail_before_any_device_work(L):
+    from paper_2002_10991_gb300.api import Problem
+
+    EINVAL = 1
+    h = ctypes.c_void_p()
+    fake = ctypes.c_void_p(16)
+    good = Problem(0, 0, 10, 4, 5, 16, 16, 16, 10)
+    arr = (Problem * 2)(good, Problem(0, 0, 10, 4, 11, 16, 16, 16, 10))  # nev > n
+    assert L.tbbt_batch_create(ctypes.byref(h), 2, ctypes.cast(arr, ctypes.c_void_p), None) == EINVAL
+    arr2 = (Problem * 1)(Problem(7, 0, 10, 4, 5, 16, 16, 16, 10))  # bad dtype
+    assert L.tbbt_batch_create(ctypes.byref(h), 1, ctypes.cast(arr2, ctypes.c_void_p), None) == EINVAL
+    arr3 = (Problem * 1)(Problem(1, 0, 10, 4, 5, 16, 16, 24, 10))  # complex q not 16-byte aligned
+    assert L.tbbt_batch_create(ctypes.byref(h), 1, ctypes.cast(arr3, ctypes.c_void_p), None) == EINVAL
+    assert L.tbbt_batch_create(ctypes.byref(h), 0, fake, None) == EINVAL
+    assert L.tbbt_batch_create(None, 1, fake, None) == EINVAL
+    assert L.tbbt_batch_execute(None, None) == EINVAL
+    assert L.tbbt_batch_destroy(None) == 0
