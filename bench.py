@@ -53,6 +53,29 @@ FP64_PEAK_TFLOPS = SMS * DFMA_PER_CLK_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "apply_kernel_traffic.json")
 
 
+def bf16_peak():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except Exception:
+        return 1900.0  # fallback figure of the profiling recipe
+
+
+BF16_PEAK_TFLOPS = bf16_peak()
+
+
+def split_tensor_flops(w):
+    """BF16 tensor-core flops the split form issues per step: per WY block of
+    32 reflectors and per column, 26 digit-pair products each of (32 x RP) and
+    (RP x 32) with RP = b + 31 rounded up to 16 (2 flops per multiply-add)."""
+    n, b, nev = w["n"], w["b"], w["nev"]
+    nb, pairs = 32, 26
+    rp = (b + nb - 1 + 15) // 16 * 16
+    J = (n - 2 + b - 1) // b if n >= 3 else 0
+    blocks = sum((n - 3 - j * b + 1 + nb - 1) // nb for j in range(J))
+    strips = (nev + 63) // 64
+    return blocks * strips * 64 * pairs * 2 * (2 * nb * rp)
+
+
 BATCH_WORKLOAD = "batch-64-mixed"
 
 
@@ -301,6 +324,9 @@ def main():
                     help="named workload (default: the benchmark workload; others are for profiler captures "
                          "and the batched-form measurement)")
     ap.add_argument("--autotune", action="store_true", help="batched workload: tune the launch geometry first")
+    ap.add_argument("--variant", default="fp64", choices=["fp64", "split"],
+                    help="fp64: reflector-by-reflector FP64 kernel; split: WY blocks on BF16 tensor cores "
+                         "with exact digit slices (real b=32/64), timed against fp64 in the same run")
     args = ap.parse_args()
     set_workload(args.workload)
     if WORKLOAD == BATCH_WORKLOAD:
@@ -341,7 +367,8 @@ def main():
     dt = torch.from_numpy(tau).cuda()
     q = torch.from_numpy(X.T.copy()).cuda().t()
     stream = torch.cuda.current_stream()
-    plan = P.Plan(cplx, n, b, nev)
+    split = args.variant == "split"
+    plan = P.Plan(cplx, n, b, nev, variant=1 if split else 0)
     info = plan.info()
 
     # parity pass on the pristine block (columns checked by the CPU baseline)
@@ -387,15 +414,47 @@ def main():
     ms_per_step = total_ms / args.steps
     value = flops * args.steps * world / (total_ms * 1e-3) / 1e12
 
+    fp64_cmp = None
+    if split:
+        ref = P.Plan(cplx, n, b, nev)
+        ref.set_reflectors(dv, dt)
+        qr = q.clone()
+        ref.execute(qr)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ref.set_reflectors(dv, dt)
+        ref.execute(qr)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp64_ms = e0.elapsed_time(e1)
+        fp64_cmp = {"fp64_ms_per_step": fp64_ms, "speedup_vs_fp64": fp64_ms / ms_per_step}
+        ref.close()
+        del qr
+
     # end to end through the host-buffer C ABI (pinned host memory, copies inside)
     hv = torch.from_numpy(v).pin_memory()
     ht = torch.from_numpy(tau).pin_memory()
     hq = torch.from_numpy(X.T.copy()).pin_memory().t()
-    P.trans_ev_tridi_to_band_host(hv, ht, n, b, nev, hq)  # warm (allocates the cached copies)
+    if split:
+        # the plan API with host-side copies around it (the one-shot host call runs the FP64 kernel)
+        def e2e_step():
+            dv.copy_(hv, non_blocking=True)
+            dt.copy_(ht, non_blocking=True)
+            q.copy_(hq, non_blocking=True)
+            plan.set_reflectors(dv, dt)
+            plan.execute(q)
+            hq.copy_(q, non_blocking=True)
+        api = "tbbt_plan_set_reflectors + tbbt_plan_execute (split variant), pinned host copies"
+    else:
+        def e2e_step():
+            P.trans_ev_tridi_to_band_host(hv, ht, n, b, nev, hq, synchronize=False)
+        api = "tbbt_trans_ev_tridi_to_band_host_z" if cplx else "tbbt_trans_ev_tridi_to_band_host_d"
+    e2e_step()  # warm (allocates the cached copies)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        P.trans_ev_tridi_to_band_host(hv, ht, n, b, nev, hq, synchronize=False)
+        e2e_step()
     P.stream_check()
     e2e_s = time.perf_counter() - t0
     if world > 1:
@@ -404,8 +463,7 @@ def main():
         e2e_s = float(tt.item())
     e2e = {"value": flops * args.e2e_steps * world / e2e_s / 1e12, "unit": "TFLOP/s",
            "h2d_bytes_per_step": int(v.nbytes + tau.nbytes + n * nev * es), "d2h_bytes_per_step": int(n * nev * es),
-           "steps": args.e2e_steps,
-           "api": "tbbt_trans_ev_tridi_to_band_host_z" if cplx else "tbbt_trans_ev_tridi_to_band_host_d"}
+           "steps": args.e2e_steps, "api": api}
 
     if rank == 0:
         apply_avg = sum(apply_ms) / len(apply_ms)
@@ -415,7 +473,7 @@ def main():
         if cs["sm_mhz"]:
             peak_at_clock = SMS * DFMA_PER_CLK_SM * 2 * cs["sm_mhz"] * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": recorded_traffic(),
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None if split else recorded_traffic(),
                 "kernel": "tbbt::apply_kernel<zdouble, 0>" if cplx else f"tbbt::apply_kernel<double, {b if b in (32, 64) else 0}>",
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe; DFMA probe 1.198 TF)",
                 "peak_at_sampled_clock": peak_at_clock,
@@ -425,14 +483,25 @@ def main():
                "kind": "oracle",
                "sample": f"{len(cols)} of {nev} columns, all {len(tau)} reflectors",
                "parity_max_abs_vs_gpu": float(np.abs(Zo - gpu_cols).max())}
+        if split:
+            # the BF16 tensor-core form: FP64-equivalent algorithmic rate; its own roofline is the
+            # tensor pipe (bf16 MMA issued per step), reported beside the FP64 reference
+            tensor_flops = split_tensor_flops(w)
+            roof.update({"bound": "tensor", "kernel": f"tbbt::split::split_apply_kernel<{b}>",
+                         "achieved": tensor_flops / (apply_avg * 1e-3) / 1e12, "peak": BF16_PEAK_TFLOPS,
+                         "frac": tensor_flops / (apply_avg * 1e-3) / 1e12 / BF16_PEAK_TFLOPS,
+                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS bf16 GEMM burst)",
+                         "fp64_equivalent_tflops": achieved, "tensor_flops_per_step": tensor_flops})
         line = {
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dtype_name(w), "data": "synthetic", "config": config_dict(w),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
             "clocks": cs, "relayout_ms_avg": sum(relayout_ms) / len(relayout_ms), "apply_ms_avg": apply_avg,
-            "launch": info,
+            "launch": info, "variant": "split_bf16" if split else "fp64",
         }
+        if fp64_cmp:
+            line.update(fp64_cmp)
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:

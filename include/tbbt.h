@@ -130,8 +130,21 @@ typedef struct {
    * strip, group of sweeps) whose progress is never published, so that the
    * units waiting for it run into wait_timeout_ms. */
   int32_t debug_withhold_unit_plus1;
-  int32_t reserved[4];
+  /* TBBT_VARIANT_FP64 (0, default): reflector-by-reflector FP64 arithmetic.
+   * TBBT_VARIANT_SPLIT_BF16 (1): real data with nbw = 32 or 64 only. Blocks of
+   * 32 consecutive reflectors of a sweep are put in compact WY form
+   * (I - V T V^T, T computed in FP64 per plan by the forward recurrence) and
+   * applied as two products on BF16 tensor cores, with the eigenvector block
+   * held in 64-bit fixed point per column and split into 6 exact 8-bit digit
+   * slices (Ozaki-style; every partial sum is exact in FP32). Error relative
+   * to each column's norm ~1e-14 per block application (see the benchmark's
+   * accuracy figures). Other shapes return TBBT_ENOTSUP. */
+  int32_t variant;
+  int32_t reserved[3];
 } tbbt_options;
+
+#define TBBT_VARIANT_FP64 0
+#define TBBT_VARIANT_SPLIT_BF16 1
 
 /* Creates a plan for problems of the given type and shape (arguments as for
  * the one-shot calls). opt may be NULL. Allocates the re-laid reflector

@@ -144,17 +144,21 @@ def stream_check(stream=None):
 class Options(ctypes.Structure):
     _fields_ = [("sweeps_per_block", ctypes.c_int32), ("stages_per_step", ctypes.c_int32),
                 ("wait_timeout_ms", ctypes.c_int32), ("debug_withhold_unit_plus1", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("variant", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+VARIANT_FP64, VARIANT_SPLIT_BF16 = 0, 1
 
 
 class Plan:
     """tbbt_plan: workspace allocated once, then set_reflectors / execute."""
 
     def __init__(self, dtype_complex: bool, n: int, nbw: int, nev: int, sweeps_per_block: int = 0,
-                 stages_per_step: int = 0, wait_timeout_ms: int = 0, debug_withhold_unit: int = -1):
+                 stages_per_step: int = 0, wait_timeout_ms: int = 0, debug_withhold_unit: int = -1,
+                 variant: int = 0):
         self.n, self.nbw, self.nev, self.complex = n, nbw, nev, dtype_complex
         self._h = ctypes.c_void_p()
-        opt = Options(sweeps_per_block, stages_per_step, wait_timeout_ms, debug_withhold_unit + 1)
+        opt = Options(sweeps_per_block, stages_per_step, wait_timeout_ms, debug_withhold_unit + 1, variant)
         st = _native.load().tbbt_plan_create(ctypes.byref(self._h), COMPLEX128 if dtype_complex else REAL64,
                                              n, nbw, nev, ctypes.byref(opt))
         _check(st, "tbbt_plan_create")

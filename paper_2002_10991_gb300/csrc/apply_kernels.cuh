@@ -191,20 +191,24 @@ __device__ __forceinline__ long long globaltimer_ns() {
 
 // Bounded wait until the unit behind `flag` has released every row >= need.
 // Returns 0 when it has, 1 if the producer was abandoned, an error was
-// recorded elsewhere, or the wait timed out (which it records).
-__device__ int wait_released(const ApplyArgs &a, const int *flag, int need) {
+// recorded elsewhere, or the wait timed out (which it records in *err).
+__device__ inline int wait_released_raw(int *err, long long timeout_ns, const int *flag, int need) {
   long long t0 = globaltimer_ns();
   for (unsigned it = 0;; ++it) {
     int v = ld_acquire(flag);
     if (v == kPoison) return 1;
     if (v <= need) return 0;
-    if (*(volatile int *)a.err != 0) return 1;
-    if (globaltimer_ns() - t0 > a.timeout_ns) {
-      atomicCAS(a.err, 0, 4 /* TBBT_ETIMEOUT */);
+    if (*(volatile int *)err != 0) return 1;
+    if (globaltimer_ns() - t0 > timeout_ns) {
+      atomicCAS(err, 0, 4 /* TBBT_ETIMEOUT */);
       return 1;
     }
     __nanosleep(it < 64 ? 64 : 512);
   }
+}
+
+__device__ __forceinline__ int wait_released(const ApplyArgs &a, const int *flag, int need) {
+  return wait_released_raw(a.err, a.timeout_ns, flag, need);
 }
 
 template <typename T>

@@ -14,6 +14,7 @@
 
 #include "../../include/tbbt.h"
 #include "apply_kernels.cuh"
+#include "split_kernels.cuh"
 
 using tbbt::StoreGeom;
 using tbbt::zdouble;
@@ -103,10 +104,109 @@ struct tbbt_plan {
   unsigned *d_counter = nullptr;
   long long timeout_ns = 20000000000LL;
   int withhold = -1;
+  // split-precision variant
+  int32_t variant = TBBT_VARIANT_FP64;
+  int64_t s_blocks = 0;
+  int32_t s_units = 0, s_grid = 0, s_ring = 0;
+  size_t s_smem = 0;
+  void *d_slices = nullptr;
+  void *d_scales = nullptr;
+  int64_t *d_block_start = nullptr;
+  int32_t *d_colexp = nullptr;
+  int *d_sflags = nullptr;
   // device copies used by the host-buffer entry points (allocated on demand)
   void *d_hv = nullptr, *d_ht = nullptr, *d_q = nullptr;
   int64_t d_q_ld = 0;
 };
+
+namespace {
+
+template <int B>
+size_t split_smem_bytes(int32_t ring) {
+  using D = tbbt::split::Dims<B>;
+  return (size_t)ring * tbbt::split::ZLD * sizeof(int64_t) + (size_t)D::BLOCK_ELEMS * 2;
+}
+
+template <int B>
+tbbt_status split_setup_b(tbbt_plan *p) {
+  using namespace tbbt::split;
+  const int32_t J = p->g.num_sweeps();
+  std::vector<int64_t> start((size_t)J + 1, 0);
+  for (int32_t j = 0; j < J; ++j) start[(size_t)j + 1] = start[(size_t)j] + (p->g.imax(j) + 1 + NB - 1) / NB;
+  p->s_blocks = start[(size_t)J];
+  p->s_ring = p->g.b + 3 * NB + 8;  // ring_rows_for(b, 1, NB)
+  p->s_smem = split_smem_bytes<B>(p->s_ring);
+  const int32_t strips = (int32_t)((p->nev + WS - 1) / WS);
+  p->s_units = strips * J;
+  if (p->s_blocks == 0 || p->nev == 0) return TBBT_OK;
+  const size_t slice_bytes = (size_t)p->s_blocks * Dims<B>::BLOCK_ELEMS * sizeof(__nv_bfloat16);
+  if (cudaMalloc(&p->d_slices, slice_bytes) != cudaSuccess ||
+      cudaMalloc(&p->d_scales, sizeof(BlockScale) * (size_t)p->s_blocks) != cudaSuccess ||
+      cudaMalloc(&p->d_block_start, sizeof(int64_t) * ((size_t)J + 1)) != cudaSuccess ||
+      cudaMalloc(&p->d_colexp, sizeof(int32_t) * (size_t)p->nev) != cudaSuccess ||
+      cudaMalloc(&p->d_sflags, sizeof(int) * (size_t)p->s_units) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return TBBT_ENOMEM;
+  }
+  TBBT_CUDA_TRY(cudaMemcpy(p->d_block_start, start.data(), sizeof(int64_t) * start.size(), cudaMemcpyHostToDevice));
+  TBBT_CUDA_TRY(allow_max_dynamic_smem(split_apply_kernel<B>));
+  int dev = 0, sms = 0, per_sm = 0;
+  TBBT_CUDA_TRY(cudaGetDevice(&dev));
+  TBBT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  TBBT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, split_apply_kernel<B>, NWARPS * 32, p->s_smem));
+  if (per_sm < 1) return TBBT_ENOTSUP;
+  const int64_t resident = (int64_t)sms * per_sm;
+  p->s_grid = (int32_t)(p->s_units < resident ? p->s_units : resident);
+  return TBBT_OK;
+}
+
+tbbt_status split_setup(tbbt_plan *p) {
+  p->variant = TBBT_VARIANT_SPLIT_BF16;
+  return p->g.b == 64 ? split_setup_b<64>(p) : split_setup_b<32>(p);
+}
+
+template <int B>
+tbbt_status split_prepare(tbbt_plan *p, cudaStream_t s) {
+  if (p->s_blocks == 0 || p->nev == 0) return TBBT_OK;
+  tbbt::split::wy_prepare_kernel<B><<<(unsigned)p->s_blocks, 128, 0, s>>>(
+      (const double *)p->d_store, p->g, p->ldv, p->d_block_start, p->g.num_sweeps(), p->s_blocks,
+      (__nv_bfloat16 *)p->d_slices, (tbbt::split::BlockScale *)p->d_scales);
+  TBBT_CUDA_TRY(cudaGetLastError());
+  return TBBT_OK;
+}
+
+template <int B>
+tbbt_status split_execute(tbbt_plan *p, void *q, int64_t ldq, cudaStream_t s) {
+  using namespace tbbt::split;
+  if (p->s_blocks == 0 || p->nev == 0) return TBBT_OK;
+  const unsigned cblocks = (unsigned)((p->nev + 7) / 8);
+  to_fixed_kernel<<<cblocks, 256, 0, s>>>((double *)q, ldq, p->g.n, p->nev, p->d_colexp);
+  TBBT_CUDA_TRY(cudaGetLastError());
+  TBBT_CUDA_TRY(cudaMemsetAsync(p->d_sflags, 0x7f, sizeof(int) * (size_t)p->s_units, s));
+  TBBT_CUDA_TRY(cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned), s));
+  SplitArgs a;
+  a.q = (int64_t *)q;
+  a.ldq = ldq;
+  a.g = p->g;
+  a.nev = p->nev;
+  a.strips = (int32_t)((p->nev + WS - 1) / WS);
+  a.units = p->s_units;
+  a.ring = p->s_ring;
+  a.slices = (const __nv_bfloat16 *)p->d_slices;
+  a.scales = (const BlockScale *)p->d_scales;
+  a.block_start = p->d_block_start;
+  a.flags = p->d_sflags;
+  a.counter = p->d_counter;
+  a.err = p->d_err;
+  a.timeout_ns = p->timeout_ns;
+  split_apply_kernel<B><<<(unsigned)p->s_grid, NWARPS * 32, p->s_smem, s>>>(a);
+  TBBT_CUDA_TRY(cudaGetLastError());
+  from_fixed_kernel<<<cblocks, 256, 0, s>>>((double *)q, ldq, p->g.n, p->nev, p->d_colexp);
+  TBBT_CUDA_TRY(cudaGetLastError());
+  return TBBT_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -186,6 +286,9 @@ tbbt_status tbbt_plan_create(tbbt_plan **plan, tbbt_dtype dtype, int64_t n, int6
   if (dtype != TBBT_REAL64 && dtype != TBBT_COMPLEX128) return TBBT_EINVAL;
   tbbt_status st = check_shape(n, nbw, nev);
   if (st != TBBT_OK) return st;
+  if (opt && opt->variant != TBBT_VARIANT_FP64 && opt->variant != TBBT_VARIANT_SPLIT_BF16) return TBBT_EINVAL;
+  if (opt && opt->variant == TBBT_VARIANT_SPLIT_BF16 && (dtype != TBBT_REAL64 || (nbw != 32 && nbw != 64)))
+    return TBBT_ENOTSUP;
   tbbt_plan *p = new (std::nothrow) tbbt_plan();
   if (!p) return TBBT_ENOMEM;
   p->dtype = dtype;
@@ -277,6 +380,10 @@ tbbt_status tbbt_plan_create(tbbt_plan **plan, tbbt_dtype dtype, int64_t n, int6
     int64_t resident = (int64_t)sms * per_sm;
     p->grid = (int32_t)(p->units < resident ? p->units : resident);
   }
+  if (opt && opt->variant == TBBT_VARIANT_SPLIT_BF16) {
+    tbbt_status sst = split_setup(p);
+    if (sst != TBBT_OK) return fail(sst);
+  }
   *plan = p;
   return TBBT_OK;
 }
@@ -288,7 +395,7 @@ tbbt_status tbbt_plan_info(const tbbt_plan *p, int32_t *G, int32_t *NB, int32_t 
   if (NB) *NB = p->NB;
   if (ring) *ring = p->ring;
   if (smem) *smem = (int32_t)p->smem;
-  if (blocks) *blocks = p->grid;
+  if (blocks) *blocks = p->variant == TBBT_VARIANT_SPLIT_BF16 ? p->s_grid : p->grid;
   return TBBT_OK;
 }
 
@@ -309,6 +416,8 @@ tbbt_status tbbt_plan_set_reflectors(tbbt_plan *p, const void *hh_v, const void 
     tbbt::relayout_kernel<double><<<(unsigned)blocks, threads, 0, s>>>(
         (const double *)hh_v, (const double *)hh_tau, p->d_stage_off, p->g, p->ldv, (double *)p->d_store);
   TBBT_CUDA_TRY(cudaGetLastError());
+  if (p->variant == TBBT_VARIANT_SPLIT_BF16)
+    return p->g.b == 64 ? split_prepare<64>(p, s) : split_prepare<32>(p, s);
   return TBBT_OK;
 }
 
@@ -319,6 +428,9 @@ tbbt_status tbbt_plan_execute(tbbt_plan *p, void *q, int64_t ldq, void *stream) 
   if (!q) return TBBT_EINVAL;
   size_t es = elem_size(p->dtype);
   if ((uintptr_t)q % es) return TBBT_EINVAL;
+  if (p->variant == TBBT_VARIANT_SPLIT_BF16)
+    return p->g.b == 64 ? split_execute<64>(p, q, ldq, (cudaStream_t)stream)
+                        : split_execute<32>(p, q, ldq, (cudaStream_t)stream);
   tbbt::ApplyArgs a;
   a.vstore = p->d_store;
   a.q = q;
@@ -352,6 +464,11 @@ tbbt_status tbbt_plan_destroy(tbbt_plan *p) {
   if (p->d_stage_off) cudaFree(p->d_stage_off);
   if (p->d_flags) cudaFree(p->d_flags);
   if (p->d_counter) cudaFree(p->d_counter);
+  if (p->d_slices) cudaFree(p->d_slices);
+  if (p->d_scales) cudaFree(p->d_scales);
+  if (p->d_block_start) cudaFree(p->d_block_start);
+  if (p->d_colexp) cudaFree(p->d_colexp);
+  if (p->d_sflags) cudaFree(p->d_sflags);
   if (p->d_hv) cudaFree(p->d_hv);
   if (p->d_ht) cudaFree(p->d_ht);
   if (p->d_q) cudaFree(p->d_q);
