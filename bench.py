@@ -257,6 +257,18 @@ def run_oracle_sample(v, tau, w, Xs):
     return Z, time.perf_counter() - t0, cores
 
 
+def ranks_max(x: float, world: int, device: str = "cuda") -> float:
+    """The largest value of x over all ranks (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -407,10 +419,7 @@ def main():
     total_ms = t_begin.elapsed_time(t_end)
     apply_ms = [m.elapsed_time(z) for (a, m, z) in ev]
     relayout_ms = [a.elapsed_time(m) for (a, m, z) in ev]
-    if world > 1:
-        tt = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = ranks_max(total_ms, world)
     ms_per_step = total_ms / args.steps
     value = flops * args.steps * world / (total_ms * 1e-3) / 1e12
 
@@ -457,10 +466,7 @@ def main():
         e2e_step()
     P.stream_check()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        tt = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = ranks_max(e2e_s, world)
     e2e = {"value": flops * args.e2e_steps * world / e2e_s / 1e12, "unit": "TFLOP/s",
            "h2d_bytes_per_step": int(v.nbytes + tau.nbytes + n * nev * es), "d2h_bytes_per_step": int(n * nev * es),
            "steps": args.e2e_steps, "api": api}
