@@ -364,15 +364,36 @@ __device__ __forceinline__ void apply_stages_regwin(double (&x)[B], double *ring
       x[0] = ring_col[(int64_t)(r % ring) * 32];  // rows r+1 .. r+B-1 are already in x[1..]
     }
     const double *ent = vb + (int64_t)(sig - s) * ldv;
+    // Entries are loaded PF iterations ahead of their use (explicit software
+    // pipeline: the loads are in-order, so this is what hides their latency).
+    constexpr int PF = 4;
     double acc = x[0];
+    {
+      double v[PF];
 #pragma unroll
-    for (int32_t t = 1; t < B; ++t) acc = fma(lds_f64(ent + t), x[t], acc);
+      for (int k = 0; k < PF; ++k) v[k] = (1 + k < B) ? lds_f64(ent + 1 + k) : 0.0;
+#pragma unroll
+      for (int32_t t = 1; t < B; ++t) {
+        const double vt = v[(t - 1) % PF];
+        if (t + PF < B) v[(t - 1) % PF] = lds_f64(ent + t + PF);
+        acc = fma(vt, x[t], acc);
+      }
+    }
     const double u = lds_f64(ent) * acc;
     if (s > 0) {
-      const double out = fma(-u, lds_f64(ent + B - 1), x[B - 1]);  // row r+B-1 leaves the window
+      // entries in the order the bottom-up update uses them: ent[B-1], ent[B-2], ..., ent[1]
+      double w[PF];
+#pragma unroll
+      for (int k = 0; k < PF; ++k) w[k] = lds_f64(ent + B - 1 - k);
+      const double out = fma(-u, w[0], x[B - 1]);  // row r+B-1 leaves the window
+      if (PF <= B - 2) w[0] = lds_f64(ent + B - 1 - PF);
       if (r + B - 1 < g.n) ring_col[(int64_t)((r + B - 1) % ring) * 32] = out;
 #pragma unroll
-      for (int32_t t = B - 1; t > 1; --t) x[t] = fma(-u, lds_f64(ent + t - 1), x[t - 1]);
+      for (int32_t k = 1; k <= B - 2; ++k) {  // element t = B - k takes entry ent[t-1]
+        const double wk = w[k % PF];
+        if (k + PF <= B - 2) w[k % PF] = lds_f64(ent + B - 1 - k - PF);
+        x[B - k] = fma(-u, wk, x[B - k - 1]);
+      }
       x[1] = x[0] - u;
     } else {
       // stage 0 ends the sweep: update in place; the whole window is final

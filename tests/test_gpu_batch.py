@@ -115,3 +115,25 @@ def test_batch_autotune_and_cache(P, tmp_path):
     for (dv, dt, n, b, nev, q), (v, tau, X) in zip(probs2, host2):
         assert np.abs(q.cpu().numpy() - oracle_result(v, tau, n, b, X)).max() <= TOL
     b2.close()
+
+
+def test_batch_full_size_64_mixed_sampled_columns(P):
+    # the batched workload: 64 problems, N in [1000, 6000], nev = N/2, b = 32, half complex
+    specs = I.batch_workload()
+    probs, host = [], []
+    for s in specs:
+        n, b, nev, c = s["n"], s["b"], s["nev"], s["complex_"]
+        v, tau = I.synthetic_store(n, b, s["seed"], c)
+        X = I.eigvec_block(n, nev, s["seed"] + 1, c)
+        probs.append((torch.from_numpy(v).cuda(), torch.from_numpy(tau).cuda(), n, b, nev, col_major(X)))
+        host.append((v, tau, X))
+    batch = P.Batch(probs)
+    batch.execute()
+    P.stream_check()
+    rng = np.random.default_rng(11)
+    for (dv, dt, n, b, nev, q), (v, tau, X) in zip(probs, host):
+        cols = np.unique(np.concatenate([[0, nev - 1], rng.choice(nev, 1)]))
+        got = q[:, torch.from_numpy(cols).cuda()].cpu().numpy()
+        Zo = oracle.back_transform(v, tau, n, b, np.asfortranarray(X[:, cols]), nthreads=oracle.num_cpus())
+        assert np.abs(got - Zo).max() <= TOL, (n, b, nev)
+    batch.close()

@@ -94,3 +94,18 @@ def test_split_rejects_unsupported_shapes(P):
     assert ei.value.status == 5
     with pytest.raises(P.TbbtError):
         P.Plan(False, 100, 16, 10, variant=SPLIT)
+
+
+def test_split_full_size_n32768_sampled_columns(P):
+    # the precision form's own workload: n=32768, b=64, nev=0.3 n
+    w = I.WORKLOADS["real-n32768-b64-dft"]
+    n, b, nev = w["n"], w["b"], w["nev"]
+    v, tau = I.synthetic_store(n, b, w["seed"], False)
+    X = I.eigvec_block(n, nev, w["seed"], False)
+    Zs = run_split(P, v, tau, n, b, X)
+    rng = np.random.default_rng(7)
+    cols = np.unique(np.concatenate([[0, 63, 64, nev - 1], rng.choice(nev, 4, replace=False)]))
+    Zo = oracle.back_transform(v, tau, n, b, np.asfortranarray(X[:, cols]), nthreads=oracle.num_cpus())
+    assert np.abs(Zs[:, cols] - Zo).max() <= TOL
+    ratio = np.linalg.norm(Zs, axis=0) / np.linalg.norm(X, axis=0)
+    assert np.abs(ratio - 1).max() <= 1e-12
