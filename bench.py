@@ -76,6 +76,26 @@ def split_tensor_flops(w):
     return blocks * strips * 64 * pairs * 2 * (2 * nb * rp)
 
 
+def tc_tensor_flops(w):
+    """BF16 tensor-core flops the tcgen05 split form issues per step: per WY
+    block (blocks aligned to stages 32k..32k+31) and per 128-column strip, 26
+    digit-pair products in each of the two contractions, each 128 x 32 x RP
+    (RP = b + 31 rounded up to 32; 2 flops per multiply-add)."""
+    n, b, nev = w["n"], w["b"], w["nev"]
+    nb, pairs = 32, 26
+    rp = (b + nb - 1 + 31) // 32 * 32
+    J = (n - 2 + b - 1) // b if n >= 3 else 0
+    blocks = sum((n - 3 - j * b) // nb + 1 for j in range(J))
+    strips = (nev + 127) // 128
+    return blocks * strips * 2 * pairs * 2 * (128 * nb * rp)
+
+
+VARIANTS = {"fp64": 0, "split": 1, "split-tc": 2}
+# our kernels per timed step: re-layout (+ per-plan preparation), apply (+ the fixed-point conversions)
+LAUNCHES_PER_STEP = {"fp64": 2, "split": 5, "split-tc": 5}
+SPLIT_KERNEL = {"split": "tbbt::split::split_apply_kernel<{b}>", "split-tc": "tbbt::tcs::tc_apply_kernel<{b}>"}
+
+
 BATCH_WORKLOAD = "batch-64-mixed"
 
 
@@ -336,9 +356,11 @@ def main():
                     help="named workload (default: the benchmark workload; others are for profiler captures "
                          "and the batched-form measurement)")
     ap.add_argument("--autotune", action="store_true", help="batched workload: tune the launch geometry first")
-    ap.add_argument("--variant", default="fp64", choices=["fp64", "split"],
+    ap.add_argument("--variant", default="fp64", choices=list(VARIANTS),
                     help="fp64: reflector-by-reflector FP64 kernel; split: WY blocks on BF16 tensor cores "
-                         "with exact digit slices (real b=32/64), timed against fp64 in the same run")
+                         "with exact digit slices (real b=32/64, warp-level mma.sync); split-tc: the same "
+                         "on tcgen05 with accumulators in tensor memory; split forms are timed against fp64 "
+                         "in the same run")
     args = ap.parse_args()
     set_workload(args.workload)
     if WORKLOAD == BATCH_WORKLOAD:
@@ -379,8 +401,8 @@ def main():
     dt = torch.from_numpy(tau).cuda()
     q = torch.from_numpy(X.T.copy()).cuda().t()
     stream = torch.cuda.current_stream()
-    split = args.variant == "split"
-    plan = P.Plan(cplx, n, b, nev, variant=1 if split else 0)
+    split = args.variant != "fp64"
+    plan = P.Plan(cplx, n, b, nev, variant=VARIANTS[args.variant])
     info = plan.info()
 
     # parity pass on the pristine block (columns checked by the CPU baseline)
@@ -454,7 +476,7 @@ def main():
             plan.set_reflectors(dv, dt)
             plan.execute(q)
             hq.copy_(q, non_blocking=True)
-        api = "tbbt_plan_set_reflectors + tbbt_plan_execute (split variant), pinned host copies"
+        api = f"tbbt_plan_set_reflectors + tbbt_plan_execute ({args.variant} variant), pinned host copies"
     else:
         def e2e_step():
             P.trans_ev_tridi_to_band_host(hv, ht, n, b, nev, hq, synchronize=False)
@@ -492,8 +514,8 @@ def main():
         if split:
             # the BF16 tensor-core form: FP64-equivalent algorithmic rate; its own roofline is the
             # tensor pipe (bf16 MMA issued per step), reported beside the FP64 reference
-            tensor_flops = split_tensor_flops(w)
-            roof.update({"bound": "tensor", "kernel": f"tbbt::split::split_apply_kernel<{b}>",
+            tensor_flops = tc_tensor_flops(w) if args.variant == "split-tc" else split_tensor_flops(w)
+            roof.update({"bound": "tensor", "kernel": SPLIT_KERNEL[args.variant].format(b=b),
                          "achieved": tensor_flops / (apply_avg * 1e-3) / 1e12, "peak": BF16_PEAK_TFLOPS,
                          "frac": tensor_flops / (apply_avg * 1e-3) / 1e12 / BF16_PEAK_TFLOPS,
                          "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS bf16 GEMM burst)",
@@ -502,9 +524,9 @@ def main():
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dtype_name(w), "data": "synthetic", "config": config_dict(w),
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": LAUNCHES_PER_STEP[args.variant] * args.steps,
             "clocks": cs, "relayout_ms_avg": sum(relayout_ms) / len(relayout_ms), "apply_ms_avg": apply_avg,
-            "launch": info, "variant": "split_bf16" if split else "fp64",
+            "launch": info, "variant": {"fp64": "fp64", "split": "split_bf16", "split-tc": "split_bf16_tc"}[args.variant],
         }
         if fp64_cmp:
             line.update(fp64_cmp)

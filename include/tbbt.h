@@ -138,13 +138,21 @@ typedef struct {
    * held in 64-bit fixed point per column and split into 6 exact 8-bit digit
    * slices (Ozaki-style; every partial sum is exact in FP32). Error relative
    * to each column's norm ~1e-14 per block application (see the benchmark's
-   * accuracy figures). Other shapes return TBBT_ENOTSUP. */
+   * accuracy figures). Other shapes return TBBT_ENOTSUP.
+   * TBBT_VARIANT_SPLIT_BF16_TC (2): the same split-precision method on the
+   * fifth-generation tensor cores (tcgen05 MMA, accumulators in tensor
+   * memory, operands staged by the bulk-copy engine): one thread block per SM
+   * owning 128-column strips, the eigenvector window held in registers.
+   * Real data with nbw = 32 or 64 on an sm_100-family device; otherwise
+   * TBBT_ENOTSUP. The plan also holds a 64-bit fixed-point copy of the
+   * eigenvector block (nev * (n + 2) * 8 bytes). */
   int32_t variant;
   int32_t reserved[3];
 } tbbt_options;
 
 #define TBBT_VARIANT_FP64 0
 #define TBBT_VARIANT_SPLIT_BF16 1
+#define TBBT_VARIANT_SPLIT_BF16_TC 2
 
 /* Creates a plan for problems of the given type and shape (arguments as for
  * the one-shot calls). opt may be NULL. Allocates the re-laid reflector

@@ -147,7 +147,7 @@ class Options(ctypes.Structure):
                 ("variant", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
-VARIANT_FP64, VARIANT_SPLIT_BF16 = 0, 1
+VARIANT_FP64, VARIANT_SPLIT_BF16, VARIANT_SPLIT_BF16_TC = 0, 1, 2
 
 
 class Plan:

@@ -15,6 +15,7 @@
 #include "../../include/tbbt.h"
 #include "apply_kernels.cuh"
 #include "split_kernels.cuh"
+#include "tc_split.cuh"
 
 using tbbt::StoreGeom;
 using tbbt::zdouble;
@@ -114,6 +115,8 @@ struct tbbt_plan {
   int64_t *d_block_start = nullptr;
   int32_t *d_colexp = nullptr;
   int *d_sflags = nullptr;
+  int64_t *d_zfix = nullptr;  // tensor-core form: fixed-point copy of the eigenvector block
+  int64_t ldz = 0;
   // device copies used by the host-buffer entry points (allocated on demand)
   void *d_hv = nullptr, *d_ht = nullptr, *d_q = nullptr;
   int64_t d_q_ld = 0;
@@ -206,6 +209,92 @@ tbbt_status split_execute(tbbt_plan *p, void *q, int64_t ldq, cudaStream_t s) {
   return TBBT_OK;
 }
 
+
+// tensor-core (tcgen05) form of the split-precision variant
+template <int B>
+tbbt_status tc_setup_b(tbbt_plan *p) {
+  using namespace tbbt::tcs;
+  using D = Geo<B>;
+  int dev = 0, major = 0, sms = 0, per_sm = 0;
+  TBBT_CUDA_TRY(cudaGetDevice(&dev));
+  TBBT_CUDA_TRY(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
+  if (major != 10) return TBBT_ENOTSUP;
+  const int32_t J = p->g.num_sweeps();
+  std::vector<int64_t> start((size_t)J + 1, 0);
+  for (int32_t j = 0; j < J; ++j) start[(size_t)j + 1] = start[(size_t)j] + p->g.imax(j) / NB + 1;
+  p->s_blocks = start[(size_t)J];
+  p->s_smem = D::SMEM;
+  const int32_t strips = (int32_t)((p->nev + WS - 1) / WS);
+  p->s_units = strips * J;
+  p->ldz = ((int64_t)p->g.n + 3) & ~(int64_t)1;  // even, >= n + 2
+  if (p->s_blocks == 0 || p->nev == 0) return TBBT_OK;
+  if (cudaMalloc(&p->d_slices, (size_t)p->s_blocks * D::BLOCK_BYTES) != cudaSuccess ||
+      cudaMalloc(&p->d_scales, sizeof(int32_t) * (size_t)p->s_blocks) != cudaSuccess ||
+      cudaMalloc(&p->d_block_start, sizeof(int64_t) * ((size_t)J + 1)) != cudaSuccess ||
+      cudaMalloc(&p->d_colexp, sizeof(int32_t) * (size_t)p->nev) != cudaSuccess ||
+      cudaMalloc(&p->d_sflags, sizeof(int) * (size_t)p->s_units) != cudaSuccess ||
+      cudaMalloc(&p->d_zfix, sizeof(int64_t) * (size_t)p->nev * (size_t)p->ldz) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return TBBT_ENOMEM;
+  }
+  TBBT_CUDA_TRY(cudaMemset(p->d_zfix, 0, sizeof(int64_t) * (size_t)p->nev * (size_t)p->ldz));
+  TBBT_CUDA_TRY(cudaMemcpy(p->d_block_start, start.data(), sizeof(int64_t) * start.size(), cudaMemcpyHostToDevice));
+  TBBT_CUDA_TRY(allow_max_dynamic_smem(tc_apply_kernel<B>));
+  TBBT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  TBBT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_apply_kernel<B>, D::NTHREADS, p->s_smem));
+  if (per_sm < 1) return TBBT_ENOTSUP;
+  // one block per SM: each holds all 512 columns of its SM's tensor memory
+  p->s_grid = (int32_t)(p->s_units < sms ? p->s_units : sms);
+  return TBBT_OK;
+}
+
+tbbt_status tc_setup(tbbt_plan *p) {
+  p->variant = TBBT_VARIANT_SPLIT_BF16_TC;
+  return p->g.b == 64 ? tc_setup_b<64>(p) : tc_setup_b<32>(p);
+}
+
+template <int B>
+tbbt_status tc_prepare(tbbt_plan *p, cudaStream_t s) {
+  if (p->s_blocks == 0 || p->nev == 0) return TBBT_OK;
+  tbbt::tcs::tc_prepare_kernel<B><<<(unsigned)p->s_blocks, 128, 0, s>>>(
+      (const double *)p->d_store, p->g, p->ldv, p->d_block_start, p->g.num_sweeps(), p->s_blocks,
+      (unsigned char *)p->d_slices, (int32_t *)p->d_scales);
+  TBBT_CUDA_TRY(cudaGetLastError());
+  return TBBT_OK;
+}
+
+template <int B>
+tbbt_status tc_execute(tbbt_plan *p, void *q, int64_t ldq, cudaStream_t s) {
+  using namespace tbbt::tcs;
+  using D = Geo<B>;
+  if (p->s_blocks == 0 || p->nev == 0) return TBBT_OK;
+  const unsigned cblocks = (unsigned)((p->nev + 7) / 8);
+  to_fixed_kernel<<<cblocks, 256, 0, s>>>((const double *)q, ldq, p->d_zfix, p->ldz, p->g.n, p->nev, p->d_colexp);
+  TBBT_CUDA_TRY(cudaGetLastError());
+  TBBT_CUDA_TRY(cudaMemsetAsync(p->d_sflags, 0x7f, sizeof(int) * (size_t)p->s_units, s));
+  TBBT_CUDA_TRY(cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned), s));
+  TcArgs a;
+  a.z = p->d_zfix;
+  a.ldz = p->ldz;
+  a.g = p->g;
+  a.nev = p->nev;
+  a.strips = (int32_t)((p->nev + WS - 1) / WS);
+  a.units = p->s_units;
+  a.slices = (const unsigned char *)p->d_slices;
+  a.gvs = (const int32_t *)p->d_scales;
+  a.block_start = p->d_block_start;
+  a.flags = p->d_sflags;
+  a.counter = p->d_counter;
+  a.err = p->d_err;
+  a.timeout_ns = p->timeout_ns;
+  a.withhold = p->withhold;
+  tc_apply_kernel<B><<<(unsigned)p->s_grid, D::NTHREADS, p->s_smem, s>>>(a);
+  TBBT_CUDA_TRY(cudaGetLastError());
+  from_fixed_kernel<<<cblocks, 256, 0, s>>>((double *)q, ldq, p->d_zfix, p->ldz, p->g.n, p->nev, p->d_colexp);
+  TBBT_CUDA_TRY(cudaGetLastError());
+  return TBBT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -286,8 +375,10 @@ tbbt_status tbbt_plan_create(tbbt_plan **plan, tbbt_dtype dtype, int64_t n, int6
   if (dtype != TBBT_REAL64 && dtype != TBBT_COMPLEX128) return TBBT_EINVAL;
   tbbt_status st = check_shape(n, nbw, nev);
   if (st != TBBT_OK) return st;
-  if (opt && opt->variant != TBBT_VARIANT_FP64 && opt->variant != TBBT_VARIANT_SPLIT_BF16) return TBBT_EINVAL;
-  if (opt && opt->variant == TBBT_VARIANT_SPLIT_BF16 && (dtype != TBBT_REAL64 || (nbw != 32 && nbw != 64)))
+  if (opt && opt->variant != TBBT_VARIANT_FP64 && opt->variant != TBBT_VARIANT_SPLIT_BF16 &&
+      opt->variant != TBBT_VARIANT_SPLIT_BF16_TC)
+    return TBBT_EINVAL;
+  if (opt && opt->variant != TBBT_VARIANT_FP64 && (dtype != TBBT_REAL64 || (nbw != 32 && nbw != 64)))
     return TBBT_ENOTSUP;
   tbbt_plan *p = new (std::nothrow) tbbt_plan();
   if (!p) return TBBT_ENOMEM;
@@ -384,6 +475,10 @@ tbbt_status tbbt_plan_create(tbbt_plan **plan, tbbt_dtype dtype, int64_t n, int6
     tbbt_status sst = split_setup(p);
     if (sst != TBBT_OK) return fail(sst);
   }
+  if (opt && opt->variant == TBBT_VARIANT_SPLIT_BF16_TC) {
+    tbbt_status sst = tc_setup(p);
+    if (sst != TBBT_OK) return fail(sst);
+  }
   *plan = p;
   return TBBT_OK;
 }
@@ -395,7 +490,7 @@ tbbt_status tbbt_plan_info(const tbbt_plan *p, int32_t *G, int32_t *NB, int32_t 
   if (NB) *NB = p->NB;
   if (ring) *ring = p->ring;
   if (smem) *smem = (int32_t)p->smem;
-  if (blocks) *blocks = p->variant == TBBT_VARIANT_SPLIT_BF16 ? p->s_grid : p->grid;
+  if (blocks) *blocks = p->variant != TBBT_VARIANT_FP64 ? p->s_grid : p->grid;
   return TBBT_OK;
 }
 
@@ -418,6 +513,8 @@ tbbt_status tbbt_plan_set_reflectors(tbbt_plan *p, const void *hh_v, const void 
   TBBT_CUDA_TRY(cudaGetLastError());
   if (p->variant == TBBT_VARIANT_SPLIT_BF16)
     return p->g.b == 64 ? split_prepare<64>(p, s) : split_prepare<32>(p, s);
+  if (p->variant == TBBT_VARIANT_SPLIT_BF16_TC)
+    return p->g.b == 64 ? tc_prepare<64>(p, s) : tc_prepare<32>(p, s);
   return TBBT_OK;
 }
 
@@ -431,6 +528,9 @@ tbbt_status tbbt_plan_execute(tbbt_plan *p, void *q, int64_t ldq, void *stream) 
   if (p->variant == TBBT_VARIANT_SPLIT_BF16)
     return p->g.b == 64 ? split_execute<64>(p, q, ldq, (cudaStream_t)stream)
                         : split_execute<32>(p, q, ldq, (cudaStream_t)stream);
+  if (p->variant == TBBT_VARIANT_SPLIT_BF16_TC)
+    return p->g.b == 64 ? tc_execute<64>(p, q, ldq, (cudaStream_t)stream)
+                        : tc_execute<32>(p, q, ldq, (cudaStream_t)stream);
   tbbt::ApplyArgs a;
   a.vstore = p->d_store;
   a.q = q;
@@ -469,6 +569,7 @@ tbbt_status tbbt_plan_destroy(tbbt_plan *p) {
   if (p->d_block_start) cudaFree(p->d_block_start);
   if (p->d_colexp) cudaFree(p->d_colexp);
   if (p->d_sflags) cudaFree(p->d_sflags);
+  if (p->d_zfix) cudaFree(p->d_zfix);
   if (p->d_hv) cudaFree(p->d_hv);
   if (p->d_ht) cudaFree(p->d_ht);
   if (p->d_q) cudaFree(p->d_q);

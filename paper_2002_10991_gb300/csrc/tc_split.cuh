@@ -1,0 +1,805 @@
+// Split-precision WY application on the fifth-generation tensor cores:
+// tcgen05.mma with BF16 digit operands in shared memory and FP32 accumulators
+// in tensor memory (TMEM), operand tiles brought in by the bulk-copy engine.
+//
+// Same method as split_kernels.cuh (compact WY blocks of 32 reflectors,
+// Z <- Z - U (V^T Z), exact digit products summed per level in FP32, levels
+// combined in 64-bit integers), laid out for one CTA per SM that owns a strip
+// of 128 columns of the eigenvector block:
+//
+//  * Z stays in registers. The block window (R = b + 31 rows, padded to 32 P
+//    rows, P = 3 for b = 64 and 2 for b = 32) is cut into P parts of 32 rows;
+//    thread group g (4 warps, one column per thread) holds part (g + t) mod P
+//    of block t. Consecutive blocks of a sweep start 32 rows apart (blocks
+//    are aligned to stages 32k .. 32k+31), so from one block to the next each
+//    part moves down one place and the group of the part that leaves the
+//    window stores it and takes the 32 new rows on top: no data moves between
+//    threads.
+//  * GEMM1 W^T = Z^T V' runs as M = 128 (strip columns) x N = 32 * (slices) x
+//    K = window rows: one instruction per digit of Z and K step covers every V'
+//    slice it pairs with, writing each slice into the TMEM columns of its
+//    level (level l = i + k of the 0-based digit indices, 32 columns each).
+//    The digits of Z are produced into two alternating shared-memory buffers
+//    while the tensor core consumes the previous one.
+//  * W is combined per column by the thread that owns the column (no
+//    shuffles), normalised, split into digits (the A operand of GEMM2).
+//  * GEMM2 corr^T = W^T U'^T runs per part of 32 rows (M = 128, N = 32 *
+//    slices, K = 32) into two TMEM regions used in turn; the group that owns
+//    the part reads its accumulators and subtracts the correction.
+//
+// Exactness (digit positions 61 - 8k, k = 1..6, balanced digits): Z is fixed
+// point with |Z| <= 2^61 (first digit |d| <= 256, others <= 128); V', U' and W
+// are scaled to |x| <= 2^60 so that all their digits are <= 128. A level sums
+// at most 6 digit products over K terms: GEMM1 (K <= 96) stays below 2^24 and
+// is read with an exact float->int conversion; GEMM2 (K = 32) stays below 2^22,
+// where the add-magic-number conversion is exact.
+//
+// Digits are read from the offset form Z' = Z + C (C = sum_k 128 * 2^(61-8k) +
+// 2^12): then digit k is the plain byte e_k of Z' at bit 61 - 8k and d_k =
+// e_k - 128, so a digit costs a shift, a logic op and one FADD (the byte is
+// placed in the mantissa of 2^23 and 2^23 + 128 subtracted). Z is kept in
+// registers in that form.
+//
+// Dependencies between sweeps, the work-unit queue and the bounded waits are
+// those of the FP64 kernel (one sweep of one strip per unit).
+#pragma once
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "apply_kernels.cuh"
+#include "split_kernels.cuh"
+
+namespace tbbt {
+namespace tcs {
+
+constexpr int NB = 32;       // reflectors per WY block
+constexpr int S = 6;         // digits per operand
+constexpr int LV = 7;        // levels kept (0-based l = i + k <= 6)
+constexpr int WS = 128;      // strip columns = MMA M
+constexpr int FIX = 61;      // fixed-point exponent of the eigenvector block
+constexpr int FOP = 60;      // fixed-point exponent of V', U' and normalised W
+constexpr int STG_LD = 34;   // staging row stride per column (int64; 272 bytes)
+constexpr int TMEM_COLS = 512;
+constexpr int REG_B = 224;   // second TMEM region (first one starts at column 0)
+
+// offset of the balanced-digit form: 128 at every digit position + half a unit
+// of the last digit
+constexpr long long kDigitOffset = (1LL << 60) + (1LL << 52) + (1LL << 44) + (1LL << 36) + (1LL << 28) +
+                                   (1LL << 20) + (1LL << 12);
+
+template <int B>
+struct Geo {
+  static constexpr int R = B + NB - 1;
+  static constexpr int RP = (R + 31) / 32 * 32;  // window rows, padded
+  static constexpr int P = RP / 32;              // parts of 32 rows
+  static constexpr int KS1 = RP / 16;            // K steps of GEMM1
+  static constexpr int NMATH = 4 * P * 32;       // threads of the math warps
+  static constexpr int NTHREADS = NMATH + 32;    // + the producer warp
+  static constexpr int SBO1 = (RP / 8) * 128;    // row-group stride of K = RP operands
+  static constexpr int VBYTES = S * NB * RP * 2;         // V' digits [32 i + m][r]
+  static constexpr int UCHUNK = S * NB * 32 * 2;         // U' digits of one part [32 i + rr][m]
+  static constexpr int UBYTES = P * UCHUNK;
+  static constexpr int EBYTES = 128;                     // per-row exponents of U (int8)
+  static constexpr int BLOCK_BYTES = VBYTES + UBYTES + EBYTES;
+  static constexpr int ZDIG = WS * RP * 2;               // one digit of the Z window [c][r]
+  static constexpr int WDIG = WS * NB * 2;               // one digit of W [c][m]
+  static constexpr int OFF_Z = 0;                        // two Z digit buffers
+  static constexpr int OFF_W = OFF_Z + 2 * ZDIG;         // S W digit buffers
+  static constexpr int OFF_V = OFF_W + S * WDIG;
+  static constexpr int OFF_U = OFF_V + VBYTES;
+  static constexpr int OFF_STG = OFF_U + UBYTES;
+  static constexpr int OFF_KMX = OFF_STG + WS * STG_LD * 8;  // [P][WS] partial maxima of |W|
+  static constexpr int SMEM = OFF_KMX + P * WS * 8;
+};
+
+// byte offset of element (row, k) of a K-major operand with kt values of k per
+// row, in the no-swizzle core-matrix layout: 8 x 16-byte core matrices, cores
+// adjacent in k 128 bytes apart (LBO), row groups kt/8 * 128 apart (SBO)
+__host__ __device__ constexpr int kmaj(int row, int k, int kt) {
+  return ((row >> 3) * (kt >> 3) + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+// ---------------------------------------------------------------------------
+// tcgen05, mbarrier and bulk-copy primitives (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t sbo) {
+  uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)(128 >> 4) << 16;              // leading byte offset: next core in K
+  d |= (uint64_t)((sbo & 0x3FFFF) >> 4) << 32;  // stride byte offset: next row group
+  d |= (uint64_t)1 << 46;                       // descriptor version of tcgen05
+  return d;                                     // base offset 0, no swizzle
+}
+// instruction descriptor: BF16 x BF16 -> FP32, both operands K-major, M = 128
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void named_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(count) : "memory");
+}
+
+// Bounded wait for the completion of the phase with the given parity. Gives
+// up (and sets the block's abort flag) on timeout or when another role of the
+// block has aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort, int *err,
+                                          long long timeout_ns) {
+  if (mbar_test(bar, parity)) return true;
+  const long long t0 = globaltimer_ns();
+  for (unsigned it = 1;; ++it) {
+    if (mbar_test(bar, parity)) return true;
+    if (*abort) return false;
+    if ((it & 15) == 0 && globaltimer_ns() - t0 > timeout_ns) {
+      atomicCAS(err, 0, 4 /* TBBT_ETIMEOUT */);
+      *abort = 1;
+      return false;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// digits
+// ---------------------------------------------------------------------------
+// Digit k (1-based) of a value in offset form, as the float d_k (exact).
+template <int K>
+__device__ __forceinline__ float digit_of(uint32_t lo, uint32_t hi) {
+  if constexpr (K == 1) {
+    const int32_t e = (int32_t)hi >> 21;  // bits 53.. of the offset value, signed
+    return __int_as_float(0x4B400000 + e) - 12583040.0f;  // (1.5 * 2^23 + e) - (1.5 * 2^23 + 128)
+  } else {
+    constexpr int pos = 61 - 8 * K;  // 45, 37, 29, 21, 13
+    uint32_t bits;
+    if constexpr (pos >= 32)
+      bits = hi >> (pos - 32);
+    else if constexpr (pos + 8 <= 32)
+      bits = lo >> pos;
+    else
+      bits = __funnelshift_r(lo, hi, pos);
+    return __int_as_float((int)((bits & 0xFFu) | 0x4B000000u)) - 8388736.0f;  // (2^23 + e) - (2^23 + 128)
+  }
+}
+// two floats whose low 16 bits are zero -> bf16x2 (first value in the low half)
+__device__ __forceinline__ uint32_t pack_hi16(float a, float b) {
+  return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
+}
+template <int K>
+__device__ __forceinline__ uint4 digits8(const int64_t *x) {
+  uint32_t w[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const uint64_t a = (uint64_t)x[2 * e], b = (uint64_t)x[2 * e + 1];
+    w[e] = pack_hi16(digit_of<K>((uint32_t)a, (uint32_t)(a >> 32)), digit_of<K>((uint32_t)b, (uint32_t)(b >> 32)));
+  }
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+template <int K>
+__device__ __forceinline__ void store_digits32(unsigned char *buf, int c, int rowq0, int kt, const int64_t (&z)[32]) {
+  // 32 consecutive K positions (rowq0 .. rowq0 + 31) of column c
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint4 v = digits8<K>(z + 8 * q);
+    *reinterpret_cast<uint4 *>(buf + kmaj(c, rowq0 + 8 * q, kt)) = v;
+  }
+}
+__device__ __forceinline__ void store_z_digit(int k, unsigned char *buf, int c, int rowq0, int kt,
+                                              const int64_t (&z)[32]) {
+  switch (k) {
+    case 1: store_digits32<1>(buf, c, rowq0, kt, z); break;
+    case 2: store_digits32<2>(buf, c, rowq0, kt, z); break;
+    case 3: store_digits32<3>(buf, c, rowq0, kt, z); break;
+    case 4: store_digits32<4>(buf, c, rowq0, kt, z); break;
+    case 5: store_digits32<5>(buf, c, rowq0, kt, z); break;
+    default: store_digits32<6>(buf, c, rowq0, kt, z); break;
+  }
+}
+
+// exact float -> int for integer values below 2^22 in magnitude
+__device__ __forceinline__ int32_t f2i_small(float v) { return __float_as_int(v + 12582912.0f) - 0x4B400000; }
+__device__ __forceinline__ int64_t shl_signed(int64_t x, int s) {
+  return s >= 0 ? (int64_t)((uint64_t)x << s) : (x >> (-s));
+}
+__device__ __forceinline__ int64_t shl8_add(int64_t h, int32_t v) { return (int64_t)((uint64_t)h << 8) + v; }
+
+// ---------------------------------------------------------------------------
+// per-plan preparation: FP64 T and U = V T per block, digits in the operand
+// layouts of the tensor-core kernel
+// ---------------------------------------------------------------------------
+// Blocks of sweep j cover stages 32k .. min(32k + 31, imax(j)), k = kt(j) ..
+// 0 with kt(j) = imax(j) / 32; block id = block_start[j] + (kt(j) - k).
+template <int B>
+__global__ void __launch_bounds__(128) tc_prepare_kernel(const double *__restrict__ vstore, StoreGeom g, int32_t ldv,
+                                                         const int64_t *__restrict__ block_start, int32_t J,
+                                                         int64_t nblocks, unsigned char *__restrict__ slices,
+                                                         int32_t *__restrict__ gvs) {
+  using D = Geo<B>;
+  constexpr int RP = D::RP;
+  __shared__ double sV[RP][NB + 1];  // V, later U = V T
+  __shared__ double sT[NB][NB + 1];
+  __shared__ double sy[NB];
+  __shared__ double stau[NB];
+  __shared__ double sred[4];
+  __shared__ int sgu[RP];
+  const int64_t blk = blockIdx.x;
+  if (blk >= nblocks) return;
+  int32_t lo = 0, hi = J - 1;
+  while (lo < hi) {
+    int32_t mid = (lo + hi + 1) >> 1;
+    if (block_start[mid] <= blk) lo = mid;
+    else hi = mid - 1;
+  }
+  const int32_t j = lo;
+  const int32_t kk = g.imax(j) / NB - (int32_t)(blk - block_start[j]);
+  const int32_t s_lo = kk * NB;
+  const int32_t cnt = min(NB, g.imax(j) - s_lo + 1);
+  const int tid = threadIdx.x;
+  const int64_t base = g.sweep_offset(j) + g.imax(j);  // entry of stage s: base - s
+  for (int idx = tid; idx < RP * NB; idx += blockDim.x) {
+    const int r = idx / NB, m = idx - r * NB;
+    double val = 0.0;
+    if (m < cnt) {
+      const int32_t s = s_lo + m;
+      const int32_t L = g.len(s, j);
+      const int tt = r - m;
+      if (tt == 0) val = 1.0;
+      else if (tt > 0 && tt < L) val = vstore[(base - s) * ldv + tt];
+    }
+    sV[r][m] = val;
+  }
+  for (int m = tid; m < NB; m += blockDim.x) stau[m] = m < cnt ? vstore[(base - (s_lo + m)) * ldv] : 0.0;
+  for (int idx = tid; idx < NB * NB; idx += blockDim.x) sT[idx / NB][idx % NB] = 0.0;
+  __syncthreads();
+  // compact WY of H_0 H_1 ... H_{cnt-1} (H_m of stage s_lo + m; the highest
+  // stage acts first): T_mm = tau_m, T[0:m, m] = -tau_m T[0:m, 0:m] (V^T v_m)
+  for (int m = 0; m < cnt; ++m) {
+    for (int k = tid; k < m; k += blockDim.x) {
+      double acc = 0.0;
+      for (int r = 0; r < RP; ++r) acc += sV[r][k] * sV[r][m];
+      sy[k] = acc;
+    }
+    __syncthreads();
+    for (int k = tid; k < m; k += blockDim.x) {
+      double acc = 0.0;
+      for (int l = k; l < m; ++l) acc += sT[k][l] * sy[l];
+      sT[k][m] = -stau[m] * acc;
+    }
+    if (tid == 0) sT[m][m] = stau[m];
+    __syncthreads();
+  }
+  unsigned char *out = slices + blk * (int64_t)D::BLOCK_BYTES;
+  // V' = V 2^(60 - gv), |V| <= 2^gv
+  double mx = 0.0;
+  for (int idx = tid; idx < RP * NB; idx += blockDim.x) mx = fmax(mx, fabs(sV[idx / NB][idx % NB]));
+  for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((tid & 31) == 0) sred[tid >> 5] = mx;
+  __syncthreads();
+  mx = fmax(fmax(sred[0], sred[1]), fmax(sred[2], sred[3]));
+  int gv = 0;
+  if (mx > 0.0) frexp(mx, &gv);
+  for (int idx = tid; idx < RP * NB; idx += blockDim.x) {
+    const int m = idx / RP, r = idx - m * RP;
+    int64_t x = __double2ll_rn(ldexp(sV[r][m], FOP - gv));
+    for (int sl = 1; sl <= S; ++sl)
+      *reinterpret_cast<__nv_bfloat16 *>(out + kmaj(NB * (sl - 1) + m, r, RP)) =
+          __float2bfloat16_rn((float)split::peel_digit(x, sl));
+  }
+  __syncthreads();
+  // U = V T in place (column m needs V[r][0..m]: go from the last column down)
+  for (int r = tid; r < RP; r += blockDim.x)
+    for (int m = NB - 1; m >= 0; --m) {
+      double acc = 0.0;
+      for (int k = 0; k <= m; ++k) acc += sV[r][k] * sT[k][m];
+      sV[r][m] = acc;
+    }
+  __syncthreads();
+  // U' = U 2^(60 - gu[r]) per row, |U[r][:]| <= 2^gu[r]
+  int8_t *rowexp = reinterpret_cast<int8_t *>(out + D::VBYTES + D::UBYTES);
+  for (int r = tid; r < RP; r += blockDim.x) {
+    double m2 = 0.0;
+    for (int m = 0; m < NB; ++m) m2 = fmax(m2, fabs(sV[r][m]));
+    int e = 0;
+    if (m2 > 0.0) frexp(m2, &e);
+    sgu[r] = e;
+    rowexp[r] = (int8_t)e;
+  }
+  for (int r = RP + tid; r < D::EBYTES; r += blockDim.x) rowexp[r] = 0;
+  __syncthreads();
+  for (int idx = tid; idx < RP * NB; idx += blockDim.x) {
+    const int r = idx / NB, m = idx - r * NB;
+    const int part = r >> 5, rr = r & 31;
+    int64_t x = __double2ll_rn(ldexp(sV[r][m], FOP - sgu[r]));
+    for (int sl = 1; sl <= S; ++sl)
+      *reinterpret_cast<__nv_bfloat16 *>(out + D::VBYTES + part * D::UCHUNK + kmaj(NB * (sl - 1) + rr, m, NB)) =
+          __float2bfloat16_rn((float)split::peel_digit(x, sl));
+  }
+  if (tid == 0) gvs[blk] = gv;
+}
+
+// ---------------------------------------------------------------------------
+// fixed point <-> FP64 (separate workspace: column c, row r at c * ldz + r + 1,
+// so that every 32-row part of a block window starts on a 16-byte boundary)
+// ---------------------------------------------------------------------------
+__global__ void to_fixed_kernel(const double *__restrict__ q, int64_t ldq, int64_t *__restrict__ z, int64_t ldz,
+                                int32_t n, int32_t nev, int32_t *__restrict__ col_exp) {
+  const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (c >= nev) return;
+  const double *col = q + c * ldq;
+  double ss = 0.0;
+  for (int32_t r = lane; r < n; r += 32) ss = fma(col[r], col[r], ss);
+  for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  int e = 0;
+  if (ss > 0.0) frexp(sqrt(ss), &e);
+  if (lane == 0) col_exp[c] = e;
+  int64_t *zc = z + c * ldz + 1;
+  for (int32_t r = lane; r < n; r += 32) zc[r] = __double2ll_rn(ldexp(col[r], FIX - e));
+}
+
+__global__ void from_fixed_kernel(double *__restrict__ q, int64_t ldq, const int64_t *__restrict__ z, int64_t ldz,
+                                  int32_t n, int32_t nev, const int32_t *__restrict__ col_exp) {
+  const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (c >= nev) return;
+  const int e = col_exp[c];
+  const int64_t *zc = z + c * ldz + 1;
+  double *col = q + c * ldq;
+  for (int32_t r = lane; r < n; r += 32) col[r] = ldexp(__ll2double_rn(zc[r]), e - FIX);
+}
+
+// ---------------------------------------------------------------------------
+// the apply kernel
+// ---------------------------------------------------------------------------
+struct TcArgs {
+  int64_t *z;  // fixed-point workspace (see to_fixed_kernel)
+  int64_t ldz;
+  StoreGeom g;
+  int32_t nev;
+  int32_t strips;  // ceil(nev / 128)
+  int32_t units;   // strips * sweeps
+  const unsigned char *slices;
+  const int32_t *gvs;
+  const int64_t *block_start;  // per sweep
+  int *flags;                  // per unit: lowest row final for its sweep
+  unsigned *counter;
+  int *err;
+  long long timeout_ns;
+  int withhold;  // test hook: unit that never publishes its progress (-1: none)
+};
+
+struct TcBarriers {
+  uint64_t zfull[2], zfree[2], g1, wfull, c[3], cfree, v, u, stage, drain;
+};
+
+template <int B>
+__global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a) {
+  using D = Geo<B>;
+  constexpr int P = D::P;
+  constexpr int RP = D::RP;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ TcBarriers bars;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_unit;
+  __shared__ int s_stop;
+  __shared__ volatile int s_abort;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const bool producer = warp == 4 * P;
+  const int grp = warp >> 2;                // math group (parts rotate over groups)
+  const int col = (warp & 3) * 32 + lane;   // strip column of this math thread = its TMEM lane
+  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+  const StoreGeom &g = a.g;
+
+  if (producer) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_tmem)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(&bars.zfull[0], D::NMATH);
+    mbar_init(&bars.zfull[1], D::NMATH);
+    mbar_init(&bars.zfree[0], 1);
+    mbar_init(&bars.zfree[1], 1);
+    mbar_init(&bars.g1, 1);
+    mbar_init(&bars.wfull, D::NMATH);
+    for (int p = 0; p < 3; ++p) mbar_init(&bars.c[p], 1);
+    mbar_init(&bars.cfree, 128);
+    mbar_init(&bars.v, 1);
+    mbar_init(&bars.u, 1);
+    mbar_init(&bars.stage, 1);
+    mbar_init(&bars.drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    s_abort = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+
+  // phase counters (each role counts the completions it waits for)
+  uint32_t n_z = 0;      // Z digit slices produced/consumed so far
+  uint32_t n_blk = 0;    // blocks processed so far (g1, wfull, c[*], cfree)
+  uint32_t n_v = 0, n_u = 0;  // producer: completions of the operand loads waited for
+  uint32_t n_st = 0;          // staged row loads (issued by the producer, counted by every math thread)
+  uint32_t iss_v = 0, iss_u = 0, iss_st = 0;  // producer: loads issued (for the drain)
+
+  for (;;) {
+    if (tid == 0) {
+      s_unit = (int)atomicAdd(a.counter, 1u);
+      s_stop = (*(volatile int *)a.err != 0);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const int u = s_unit;
+    if (u >= a.units || s_stop || s_abort) break;
+    const int32_t j = u / a.strips;
+    const int32_t c0 = (u - j * a.strips) * WS;
+    int *myflag = a.flags + u;
+    const int *prevflag = j > 0 ? a.flags + (u - a.strips) : nullptr;
+    const bool publish = u != a.withhold;
+    const int32_t kt = g.imax(j) / NB;  // blocks k = kt .. 0
+    const int32_t nblk = kt + 1;
+    const int32_t jb = j * g.b;
+    const int64_t blk0 = a.block_start[j];
+    auto r0_of = [&](int32_t t) { return (kt - t) * NB + 1 + jb; };  // first window row of block t
+    // every row of the first window must be final for the previous sweep
+    if (tid == 0 && prevflag && wait_released_raw(a.err, a.timeout_ns, prevflag, r0_of(0))) s_abort = 1;
+    __syncthreads();
+
+    if (!s_abort) {
+      if (producer) {
+        if (lane == 0) {
+          // ------------------------------------------------------------ producer
+          const unsigned char *blkp = a.slices + blk0 * (int64_t)D::BLOCK_BYTES;
+          mbar_expect_tx(&bars.v, D::VBYTES);
+          bulk_load(smem + D::OFF_V, blkp, D::VBYTES, &bars.v);
+          ++iss_v;
+          mbar_expect_tx(&bars.u, D::UBYTES);
+          bulk_load(smem + D::OFF_U, blkp + D::VBYTES, D::UBYTES, &bars.u);
+          ++iss_u;
+          const uint32_t zbase = smem_u32(smem + D::OFF_Z);
+          const uint32_t wbase = smem_u32(smem + D::OFF_W);
+          const uint32_t vbase = smem_u32(smem + D::OFF_V);
+          const uint32_t ubase = smem_u32(smem + D::OFF_U);
+          for (int32_t t = 0; t < nblk && !s_abort; ++t) {
+            const int32_t r0 = r0_of(t);
+            if (!mbar_wait(&bars.v, n_v & 1, &s_abort, a.err, a.timeout_ns)) break;
+            ++n_v;
+            // GEMM1: level l = i + k (0-based), 32 TMEM columns per level
+            bool ok = true;
+            for (int k = 0; k < S; ++k) {
+              const uint32_t zb = n_z & 1;
+              if (!mbar_wait(&bars.zfull[zb], (n_z >> 1) & 1, &s_abort, a.err, a.timeout_ns)) {
+                ok = false;
+                break;
+              }
+              ++n_z;
+              tc_fence_after();
+              const int ni = (S < LV - k) ? S : LV - k;  // V' slices paired with digit k
+              for (int ks = 0; ks < D::KS1; ++ks) {
+                const uint64_t ad = smem_desc(zbase + zb * D::ZDIG + ks * 256, D::SBO1);
+                const uint32_t bv = vbase + ks * 256;
+                if (k == 1 && ks == 0) {
+                  // levels 1..5 accumulate; level 6 starts here (slice 5)
+                  tc_mma(tmem + 32, ad, smem_desc(bv, D::SBO1), idesc_bf16(5 * NB), 1);
+                  tc_mma(tmem + 32 * 6, ad, smem_desc(bv + 20 * D::SBO1, D::SBO1), idesc_bf16(NB), 0);
+                } else {
+                  tc_mma(tmem + 32 * k, ad, smem_desc(bv, D::SBO1), idesc_bf16(ni * NB), (k > 0 || ks > 0) ? 1u : 0u);
+                }
+              }
+              tc_commit(&bars.zfree[zb]);
+            }
+            if (!ok) break;
+            tc_commit(&bars.g1);
+            // V' is free once GEMM1 is done: bring in the next block's
+            if (!mbar_wait(&bars.g1, n_blk & 1, &s_abort, a.err, a.timeout_ns)) break;
+            if (t + 1 < nblk) {
+              mbar_expect_tx(&bars.v, D::VBYTES);
+              bulk_load(smem + D::OFF_V, blkp + (int64_t)(t + 1) * D::BLOCK_BYTES, D::VBYTES, &bars.v);
+              ++iss_v;
+            }
+            // GEMM2 per part of 32 rows
+            if (!mbar_wait(&bars.u, n_u & 1, &s_abort, a.err, a.timeout_ns)) break;
+            ++n_u;
+            if (!mbar_wait(&bars.wfull, n_blk & 1, &s_abort, a.err, a.timeout_ns)) break;
+            tc_fence_after();
+            for (int p = 0; p < P && ok; ++p) {
+              if (p == 2) {
+                if (!mbar_wait(&bars.cfree, n_blk & 1, &s_abort, a.err, a.timeout_ns)) {
+                  ok = false;
+                  break;
+                }
+                tc_fence_after();
+              }
+              const uint32_t dreg = tmem + ((p & 1) ? 0u : (uint32_t)REG_B);
+              const uint32_t ub = ubase + p * D::UCHUNK;
+              for (int k = 0; k < S; ++k) {
+                const int ni = (S < LV - k) ? S : LV - k;
+                for (int ks = 0; ks < 2; ++ks) {
+                  const uint64_t ad = smem_desc(wbase + k * D::WDIG + ks * 256, 512);
+                  const uint32_t bu = ub + ks * 256;
+                  if (k == 1 && ks == 0) {
+                    tc_mma(dreg + 32, ad, smem_desc(bu, 512), idesc_bf16(5 * NB), 1);
+                    tc_mma(dreg + 32 * 6, ad, smem_desc(bu + 20 * 512, 512), idesc_bf16(NB), 0);
+                  } else {
+                    tc_mma(dreg + 32 * k, ad, smem_desc(bu, 512), idesc_bf16(ni * NB), (k > 0 || ks > 0) ? 1u : 0u);
+                  }
+                }
+              }
+              tc_commit(&bars.c[p]);
+            }
+            if (!ok) break;
+            // rows of the next block's new part (the previous sweep must have
+            // finished them): one bulk copy of 32 rows per column
+            if (t + 1 < nblk) {
+              const int32_t rn = r0 - NB;
+              if (prevflag && wait_released_raw(a.err, a.timeout_ns, prevflag, rn)) {
+                s_abort = 1;
+                break;
+              }
+              const int ncols = min(WS, a.nev - c0);
+              mbar_expect_tx(&bars.stage, (uint32_t)ncols * 256u);
+              for (int c = 0; c < ncols; ++c)
+                bulk_load(smem + D::OFF_STG + c * STG_LD * 8, a.z + (int64_t)(c0 + c) * a.ldz + rn + 1, 256u,
+                          &bars.stage);
+              ++iss_st;
+            }
+            // U' is free once GEMM2 is done
+            if (!mbar_wait(&bars.c[P - 1], n_blk & 1, &s_abort, a.err, a.timeout_ns)) break;
+            ++n_blk;
+            if (t + 1 < nblk) {
+              mbar_expect_tx(&bars.u, D::UBYTES);
+              bulk_load(smem + D::OFF_U, blkp + (int64_t)(t + 1) * D::BLOCK_BYTES + D::VBYTES, D::UBYTES, &bars.u);
+              ++iss_u;
+            }
+          }
+        }
+        __syncwarp();
+      } else {
+        // -------------------------------------------------------------- math
+        const int64_t C = kDigitOffset;
+        const bool colok = c0 + col < a.nev;
+        const int64_t *zcol = a.z + (int64_t)(c0 + col) * a.ldz + 1;
+        int64_t z[32];  // my part of the window, offset form
+        {
+          const int32_t rb = r0_of(0) + 32 * grp;
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const int32_t r = rb + i;
+            z[i] = (colok && r < g.n) ? (int64_t)__ldcg((const long long *)(zcol + r)) + C : C;
+          }
+        }
+        for (int32_t t = 0; t < nblk; ++t) {
+          const int32_t r0 = r0_of(t);
+          const int p = (grp + t) % P;  // my part of this block's window
+          const int64_t blk = blk0 + t;
+          // ---- digits of Z -> GEMM1
+          bool ok = true;
+          for (int k = 1; k <= S; ++k) {
+            const uint32_t zb = n_z & 1;
+            if (n_z >= 2 && !mbar_wait(&bars.zfree[zb], ((n_z >> 1) - 1) & 1, &s_abort, a.err, a.timeout_ns)) {
+              ok = false;
+              break;
+            }
+            store_z_digit(k, smem + D::OFF_Z + zb * D::ZDIG, col, 32 * p, RP, z);
+            fence_proxy_async();
+            tc_fence_before();
+            mbar_arrive(&bars.zfull[zb]);
+            ++n_z;
+          }
+          if (!ok) break;
+          // ---- W = V'^T Z for my column and my reflector range
+          if (!mbar_wait(&bars.g1, n_blk & 1, &s_abort, a.err, a.timeout_ns)) break;
+          tc_fence_after();
+          const int m0 = (P == 3) ? (grp == 0 ? 0 : (grp == 1 ? 16 : 24)) : 16 * grp;
+          const int mc = (P == 3 && grp > 0) ? 8 : 16;
+          int64_t w[16];
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            if (q * 8 < mc) {
+#pragma unroll
+              for (int l = 0; l < LV; ++l) {
+                uint32_t r[8];
+                tmem_ld8(tmem + lane_base + 32 * l + m0 + 8 * q, r);
+                tc_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                  const int32_t v = __float2int_rn(__uint_as_float(r[i]));
+                  int64_t &x = w[8 * q + i];
+                  if (l == 0) x = v;
+                  else if (l < LV - 1) x = shl8_add(x, v);
+                  else x = (int64_t)((uint64_t)x << 2) + (v >> 6);  // W = 4 h + floor(a_6 / 64)
+                }
+              }
+            } else {
+#pragma unroll
+              for (int i = 0; i < 8; ++i) w[8 * q + i] = 0;
+            }
+          }
+          uint64_t mx = 0;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const uint64_t ax = (uint64_t)(w[i] < 0 ? -w[i] : w[i]);
+            mx = ax > mx ? ax : mx;
+          }
+          uint64_t *kmx = reinterpret_cast<uint64_t *>(smem + D::OFF_KMX);
+          kmx[grp * WS + col] = mx;
+          named_sync(1, D::NMATH);
+#pragma unroll
+          for (int q = 0; q < P; ++q) {
+            const uint64_t o = kmx[q * WS + col];
+            mx = o > mx ? o : mx;
+          }
+          const int bits = mx ? 64 - __clzll((long long)mx) : 0;
+          const int kcol = (bits > 0 && bits < FOP) ? FOP - bits : 0;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) w[i] = (int64_t)((uint64_t)w[i] << kcol) + C;
+          {
+            unsigned char *wb = smem + D::OFF_W;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+              if (q * 8 < mc) {
+                const int64_t *wq = w + 8 * q;
+                const int koff = kmaj(col, m0 + 8 * q, NB);
+                *reinterpret_cast<uint4 *>(wb + 0 * D::WDIG + koff) = digits8<1>(wq);
+                *reinterpret_cast<uint4 *>(wb + 1 * D::WDIG + koff) = digits8<2>(wq);
+                *reinterpret_cast<uint4 *>(wb + 2 * D::WDIG + koff) = digits8<3>(wq);
+                *reinterpret_cast<uint4 *>(wb + 3 * D::WDIG + koff) = digits8<4>(wq);
+                *reinterpret_cast<uint4 *>(wb + 4 * D::WDIG + koff) = digits8<5>(wq);
+                *reinterpret_cast<uint4 *>(wb + 5 * D::WDIG + koff) = digits8<6>(wq);
+              }
+            }
+          }
+          fence_proxy_async();
+          tc_fence_before();
+          mbar_arrive(&bars.wfull);
+          // ---- corr of my part: Z -= sum_l B_l 2^(rs + gu[r] - 8 l)
+          if (!mbar_wait(&bars.c[p], n_blk & 1, &s_abort, a.err, a.timeout_ns)) break;
+          tc_fence_after();
+          const int gv = __ldg(a.gvs + blk);
+          const int8_t *gu = reinterpret_cast<const int8_t *>(a.slices + blk * (int64_t)D::BLOCK_BYTES + D::VBYTES +
+                                                              D::UBYTES) + 32 * p;
+          const int rs = 50 + gv - kcol;
+          const uint32_t dreg = tmem + lane_base + ((p & 1) ? 0u : (uint32_t)REG_B);
+          // levels in pairs: a_l 2^8 + a_(l+1) is exact in 32 bits (|a| < 2^22)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {  // 8 rows at a time
+            int64_t corr[8];
+            int sh[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              corr[i] = 0;
+              sh[i] = rs + (int)__ldg(gu + 8 * q + i);
+            }
+#pragma unroll
+            for (int lp = 0; lp < 4; ++lp) {
+              uint32_t ra[8], rb[8];
+              tmem_ld8(dreg + 32 * (2 * lp) + 8 * q, ra);
+              if (lp < 3) tmem_ld8(dreg + 32 * (2 * lp + 1) + 8 * q, rb);
+              tc_wait_ld();
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                int32_t pv = f2i_small(__uint_as_float(ra[i]));
+                if (lp < 3) pv = pv * 256 + f2i_small(__uint_as_float(rb[i]));
+                corr[i] += shl_signed((int64_t)pv, sh[i] - (lp < 3 ? 16 * lp + 8 : 48));
+              }
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) z[8 * q + i] -= corr[i];
+          }
+          if (P == 3 && p == 0) {
+            tc_fence_before();
+            mbar_arrive(&bars.cfree);
+          }
+          ++n_blk;
+          // ---- the part leaving the window: store it, take the new rows
+          if (t + 1 < nblk && p == P - 1) {
+            const int32_t rb = r0 + 32 * (P - 1);
+            if (colok) {
+              int64_t *dst = a.z + (int64_t)(c0 + col) * a.ldz + 1;
+#pragma unroll
+              for (int i = 0; i < 32; ++i)
+                if (rb + i < g.n) dst[rb + i] = z[i] - C;
+            }
+            __threadfence();
+            named_sync(2 + grp, 128);
+            if ((warp & 3) == 0 && lane == 0 && publish) st_release(myflag, rb);
+            if (!mbar_wait(&bars.stage, n_st & 1, &s_abort, a.err, a.timeout_ns)) break;
+            const int64_t *stg = reinterpret_cast<const int64_t *>(smem + D::OFF_STG) + col * STG_LD;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) z[i] = colok ? stg[i] + C : C;
+          }
+          if (t + 1 < nblk) ++n_st;  // every group counts every staged load
+        }
+        if (!s_abort) {
+          // the whole last window is final
+          const int32_t rb = r0_of(nblk - 1) + 32 * ((grp + nblk - 1) % P);
+          if (colok) {
+            int64_t *dst = a.z + (int64_t)(c0 + col) * a.ldz + 1;
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              if (rb + i < g.n) dst[rb + i] = z[i] - C;
+          }
+          __threadfence();
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (s_abort) break;
+    if (tid == 0 && publish) st_release(myflag, r0_of(nblk - 1));
+  }
+  // drain: no copy or MMA of this block may still be in flight at exit
+  if (s_abort && producer && lane == 0) {
+    tc_commit(&bars.drain);
+    volatile int never = 0;
+    const long long lim = 2000000000LL;
+    mbar_wait(&bars.drain, 0, &never, a.err, lim);
+    // the last load issued on each barrier has landed once its phase completed
+    if (iss_v) mbar_wait(&bars.v, (iss_v - 1) & 1, &never, a.err, lim);
+    if (iss_u) mbar_wait(&bars.u, (iss_u - 1) & 1, &never, a.err, lim);
+    if (iss_st) mbar_wait(&bars.stage, (iss_st - 1) & 1, &never, a.err, lim);
+  }
+  if (s_abort && tid == 0 && s_unit < a.units) st_release(a.flags + s_unit, kPoison);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (producer) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS)
+                             : "memory");
+}
+
+}  // namespace tcs
+}  // namespace tbbt

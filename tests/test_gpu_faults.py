@@ -50,3 +50,31 @@ def test_withheld_progress_times_out_and_context_survives(P):
     Zo = oracle.back_transform(v, tau, n, b, X.copy(order="F"))
     assert np.abs(q.cpu().numpy() - Zo).max() <= 1e-11
     good.close()
+
+
+def test_withheld_progress_times_out_tcgen05_split(P):
+    # the tensor-core split form: the unit behind the withheld one gives up at
+    # its first wait, the others abandon their units mid-way (their waits see
+    # the error word); every block drains its copies and MMAs, frees its
+    # tensor memory and exits
+    n, b, nev = 600, 64, 300  # 3 strips of 128 columns, 10 sweeps
+    v, tau = I.synthetic_store(n, b, 5, False)
+    X = I.eigvec_block(n, nev, 6, False)
+    dv, dt = torch.from_numpy(v).cuda(), torch.from_numpy(tau).cuda()
+    plan = P.Plan(False, n, b, nev, wait_timeout_ms=300, debug_withhold_unit=0, variant=2)
+    plan.set_reflectors(dv, dt)
+    q = torch.from_numpy(X.T.copy()).cuda().t()
+    plan.execute(q)
+    with pytest.raises(P.TbbtError) as ei:
+        P.stream_check()
+    assert ei.value.status == 4  # TBBT_ETIMEOUT
+    plan.close()
+    P.stream_check()
+    good = P.Plan(False, n, b, nev, variant=2)
+    good.set_reflectors(dv, dt)
+    q = torch.from_numpy(X.T.copy()).cuda().t()
+    good.execute(q)
+    P.stream_check()
+    Zo = oracle.back_transform(v, tau, n, b, X.copy(order="F"))
+    assert np.abs(q.cpu().numpy() - Zo).max() <= 1e-11
+    good.close()
