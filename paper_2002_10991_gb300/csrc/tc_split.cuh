@@ -141,6 +141,12 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
                : "r"(taddr)
                : "memory");
 }
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr)
+               : "memory");
+}
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
@@ -223,6 +229,16 @@ __device__ __forceinline__ uint4 digits8(const int64_t *x) {
     w[e] = pack_hi16(digit_of<K>((uint32_t)a, (uint32_t)(a >> 32)), digit_of<K>((uint32_t)b, (uint32_t)(b >> 32)));
   }
   return make_uint4(w[0], w[1], w[2], w[3]);
+}
+template <int K>
+__device__ __forceinline__ uint2 digits4(const int64_t *x) {
+  uint32_t w[2];
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const uint64_t a = (uint64_t)x[2 * e], b = (uint64_t)x[2 * e + 1];
+    w[e] = pack_hi16(digit_of<K>((uint32_t)a, (uint32_t)(a >> 32)), digit_of<K>((uint32_t)b, (uint32_t)(b >> 32)));
+  }
+  return make_uint2(w[0], w[1]);
 }
 template <int K>
 __device__ __forceinline__ void store_digits32(unsigned char *buf, int c, int rowq0, int kt, const int64_t (&z)[32]) {
@@ -417,6 +433,27 @@ struct TcArgs {
   int withhold;  // test hook: unit that never publishes its progress (-1: none)
 };
 
+// Levels of W = V'^T Z for C consecutive reflectors of this thread's column,
+// combined exactly (Horner in base 2^8 over levels 0..5, then the level-6
+// term): W_int = sum_l a_l 2^(42 - 8 l).
+template <int C>
+__device__ __forceinline__ void w_levels(uint32_t taddr, int64_t *w) {
+#pragma unroll
+  for (int l = 0; l < LV; ++l) {
+    uint32_t r[C];
+    if constexpr (C == 8) tmem_ld8(taddr + 32 * l, r);
+    else tmem_ld4(taddr + 32 * l, r);
+    tc_wait_ld();
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+      const int32_t v = __float2int_rn(__uint_as_float(r[i]));  // |v| < 2^24: exact
+      if (l == 0) w[i] = v;
+      else if (l < LV - 1) w[i] = shl8_add(w[i], v);
+      else w[i] = (int64_t)((uint64_t)w[i] << 2) + (v >> 6);  // 4 h + floor(a_6 / 64)
+    }
+  }
+}
+
 struct TcBarriers {
   uint64_t zfull[2], zfree[2], g1, wfull, c[3], cfree, v, u, stage, drain;
 };
@@ -440,7 +477,7 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a)
   const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
   const StoreGeom &g = a.g;
 
-  if (producer) {
+  if (warp == 4 * P) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_tmem)),
                  "r"(TMEM_COLS)
                  : "memory");
@@ -500,7 +537,7 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a)
 
     if (!s_abort) {
       if (producer) {
-        if (lane == 0) {
+        if (warp == 4 * P && lane == 0) {
           // ------------------------------------------------------------ producer
           const unsigned char *blkp = a.slices + blk0 * (int64_t)D::BLOCK_BYTES;
           mbar_expect_tx(&bars.v, D::VBYTES);
@@ -625,9 +662,21 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a)
           const int32_t r0 = r0_of(t);
           const int p = (grp + t) % P;  // my part of this block's window
           const int64_t blk = blk0 + t;
+          // per-row exponents of U for my part, and the block's V scale (read now, used late)
+          uint32_t gu4[8];
+          int gv;
+          {
+            const uint4 *gsrc = reinterpret_cast<const uint4 *>(a.slices + blk * (int64_t)D::BLOCK_BYTES + D::VBYTES +
+                                                                D::UBYTES + 32 * p);
+            const uint4 g0 = __ldg(gsrc), g1 = __ldg(gsrc + 1);
+            gu4[0] = g0.x; gu4[1] = g0.y; gu4[2] = g0.z; gu4[3] = g0.w;
+            gu4[4] = g1.x; gu4[5] = g1.y; gu4[6] = g1.z; gu4[7] = g1.w;
+            gv = __ldg(a.gvs + blk);
+          }
           // ---- digits of Z -> GEMM1
           bool ok = true;
-          for (int k = 1; k <= S; ++k) {
+#pragma unroll
+          for (int k = 1; k <= S; ++k) {  // unrolled: the digit helpers take k as a constant
             const uint32_t zb = n_z & 1;
             if (n_z >= 2 && !mbar_wait(&bars.zfree[zb], ((n_z >> 1) - 1) & 1, &s_abort, a.err, a.timeout_ns)) {
               ok = false;
@@ -643,36 +692,32 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a)
           // ---- W = V'^T Z for my column and my reflector range
           if (!mbar_wait(&bars.g1, n_blk & 1, &s_abort, a.err, a.timeout_ns)) break;
           tc_fence_after();
-          const int m0 = (P == 3) ? (grp == 0 ? 0 : (grp == 1 ? 16 : 24)) : 16 * grp;
-          const int mc = (P == 3 && grp > 0) ? 8 : 16;
-          int64_t w[16];
-#pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            if (q * 8 < mc) {
-#pragma unroll
-              for (int l = 0; l < LV; ++l) {
-                uint32_t r[8];
-                tmem_ld8(tmem + lane_base + 32 * l + m0 + 8 * q, r);
-                tc_wait_ld();
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                  const int32_t v = __float2int_rn(__uint_as_float(r[i]));
-                  int64_t &x = w[8 * q + i];
-                  if (l == 0) x = v;
-                  else if (l < LV - 1) x = shl8_add(x, v);
-                  else x = (int64_t)((uint64_t)x << 2) + (v >> 6);  // W = 4 h + floor(a_6 / 64)
-                }
-              }
-            } else {
-#pragma unroll
-              for (int i = 0; i < 8; ++i) w[8 * q + i] = 0;
-            }
+          // reflector chunks of this group: 12 / 12 / 8 (b = 64) or 16 / 16 (b = 32)
+          int ca0, cw0, ca1, cw1;
+          if (P == 3) {
+            ca0 = grp == 0 ? 0 : (grp == 1 ? 12 : 24);
+            cw0 = grp == 1 ? 4 : 8;
+            ca1 = grp == 0 ? 8 : 16;
+            cw1 = grp == 0 ? 4 : (grp == 1 ? 8 : 0);
+          } else {
+            ca0 = 16 * grp;
+            cw0 = 8;
+            ca1 = 16 * grp + 8;
+            cw1 = 8;
           }
+          int64_t w[16];
+          const uint32_t wt = tmem + lane_base;
+          if (cw0 == 8) w_levels<8>(wt + ca0, w);
+          else w_levels<4>(wt + ca0, w);
+          if (cw1 == 8) w_levels<8>(wt + ca1, w + 8);
+          else if (cw1 == 4) w_levels<4>(wt + ca1, w + 8);
           uint64_t mx = 0;
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
-            const uint64_t ax = (uint64_t)(w[i] < 0 ? -w[i] : w[i]);
-            mx = ax > mx ? ax : mx;
+            if ((i < 8 && i < cw0) || (i >= 8 && i - 8 < cw1)) {
+              const uint64_t ax = (uint64_t)(w[i] < 0 ? -w[i] : w[i]);
+              mx = ax > mx ? ax : mx;
+            }
           }
           uint64_t *kmx = reinterpret_cast<uint64_t *>(smem + D::OFF_KMX);
           kmx[grp * WS + col] = mx;
@@ -690,54 +735,73 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a)
             unsigned char *wb = smem + D::OFF_W;
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
-              if (q * 8 < mc) {
-                const int64_t *wq = w + 8 * q;
-                const int koff = kmaj(col, m0 + 8 * q, NB);
+              const int cw = q ? cw1 : cw0;
+              const int64_t *wq = w + 8 * q;
+              const int koff = kmaj(col, q ? ca1 : ca0, NB);
+              if (cw == 8) {
                 *reinterpret_cast<uint4 *>(wb + 0 * D::WDIG + koff) = digits8<1>(wq);
                 *reinterpret_cast<uint4 *>(wb + 1 * D::WDIG + koff) = digits8<2>(wq);
                 *reinterpret_cast<uint4 *>(wb + 2 * D::WDIG + koff) = digits8<3>(wq);
                 *reinterpret_cast<uint4 *>(wb + 3 * D::WDIG + koff) = digits8<4>(wq);
                 *reinterpret_cast<uint4 *>(wb + 4 * D::WDIG + koff) = digits8<5>(wq);
                 *reinterpret_cast<uint4 *>(wb + 5 * D::WDIG + koff) = digits8<6>(wq);
+              } else if (cw == 4) {
+                *reinterpret_cast<uint2 *>(wb + 0 * D::WDIG + koff) = digits4<1>(wq);
+                *reinterpret_cast<uint2 *>(wb + 1 * D::WDIG + koff) = digits4<2>(wq);
+                *reinterpret_cast<uint2 *>(wb + 2 * D::WDIG + koff) = digits4<3>(wq);
+                *reinterpret_cast<uint2 *>(wb + 3 * D::WDIG + koff) = digits4<4>(wq);
+                *reinterpret_cast<uint2 *>(wb + 4 * D::WDIG + koff) = digits4<5>(wq);
+                *reinterpret_cast<uint2 *>(wb + 5 * D::WDIG + koff) = digits4<6>(wq);
               }
             }
           }
           fence_proxy_async();
           tc_fence_before();
           mbar_arrive(&bars.wfull);
-          // ---- corr of my part: Z -= sum_l B_l 2^(rs + gu[r] - 8 l)
+          // ---- corr of my part: Z -= sum_l B_l 2^(rs + gu[r] - 8 l); levels in
+          // pairs (a_l 2^8 + a_(l+1) is exact in 32 bits, |a| < 2^22), then
+          // T = P01 2^16 + P23 and T2 = P45 2^8 + a_6 (exact in 64 bits)
           if (!mbar_wait(&bars.c[p], n_blk & 1, &s_abort, a.err, a.timeout_ns)) break;
           tc_fence_after();
-          const int gv = __ldg(a.gvs + blk);
-          const int8_t *gu = reinterpret_cast<const int8_t *>(a.slices + blk * (int64_t)D::BLOCK_BYTES + D::VBYTES +
-                                                              D::UBYTES) + 32 * p;
           const int rs = 50 + gv - kcol;
           const uint32_t dreg = tmem + lane_base + ((p & 1) ? 0u : (uint32_t)REG_B);
-          // levels in pairs: a_l 2^8 + a_(l+1) is exact in 32 bits (|a| < 2^22)
 #pragma unroll
           for (int q = 0; q < 4; ++q) {  // 8 rows at a time
-            int64_t corr[8];
-            int sh[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              corr[i] = 0;
-              sh[i] = rs + (int)__ldg(gu + 8 * q + i);
-            }
-#pragma unroll
-            for (int lp = 0; lp < 4; ++lp) {
+            int64_t t1[8], t2[8];
+            {
               uint32_t ra[8], rb[8];
-              tmem_ld8(dreg + 32 * (2 * lp) + 8 * q, ra);
-              if (lp < 3) tmem_ld8(dreg + 32 * (2 * lp + 1) + 8 * q, rb);
+              int32_t p01[8];
+              tmem_ld8(dreg + 8 * q, ra);
+              tmem_ld8(dreg + 32 + 8 * q, rb);
               tc_wait_ld();
 #pragma unroll
-              for (int i = 0; i < 8; ++i) {
-                int32_t pv = f2i_small(__uint_as_float(ra[i]));
-                if (lp < 3) pv = pv * 256 + f2i_small(__uint_as_float(rb[i]));
-                corr[i] += shl_signed((int64_t)pv, sh[i] - (lp < 3 ? 16 * lp + 8 : 48));
-              }
+              for (int i = 0; i < 8; ++i)
+                p01[i] = f2i_small(__uint_as_float(ra[i])) * 256 + f2i_small(__uint_as_float(rb[i]));
+              tmem_ld8(dreg + 64 + 8 * q, ra);
+              tmem_ld8(dreg + 96 + 8 * q, rb);
+              tc_wait_ld();
+#pragma unroll
+              for (int i = 0; i < 8; ++i)
+                t1[i] = (int64_t)((uint64_t)(int64_t)p01[i] << 16) +
+                        (f2i_small(__uint_as_float(ra[i])) * 256 + f2i_small(__uint_as_float(rb[i])));
+              tmem_ld8(dreg + 128 + 8 * q, ra);
+              tmem_ld8(dreg + 160 + 8 * q, rb);
+              tc_wait_ld();
+#pragma unroll
+              for (int i = 0; i < 8; ++i)
+                p01[i] = f2i_small(__uint_as_float(ra[i])) * 256 + f2i_small(__uint_as_float(rb[i]));
+              tmem_ld8(dreg + 192 + 8 * q, ra);
+              tc_wait_ld();
+#pragma unroll
+              for (int i = 0; i < 8; ++i)
+                t2[i] = (int64_t)((uint64_t)(int64_t)p01[i] << 8) + f2i_small(__uint_as_float(ra[i]));
             }
 #pragma unroll
-            for (int i = 0; i < 8; ++i) z[8 * q + i] -= corr[i];
+            for (int i = 0; i < 8; ++i) {
+              const int r = 8 * q + i;
+              const int sh = rs + (int)(int8_t)(gu4[r >> 2] >> (8 * (r & 3)));
+              z[r] -= shl_signed(t1[i], sh - 24) + shl_signed(t2[i], sh - 48);
+            }
           }
           if (P == 3 && p == 0) {
             tc_fence_before();
@@ -783,7 +847,7 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a)
     if (tid == 0 && publish) st_release(myflag, r0_of(nblk - 1));
   }
   // drain: no copy or MMA of this block may still be in flight at exit
-  if (s_abort && producer && lane == 0) {
+  if (s_abort && warp == 4 * P && lane == 0) {
     tc_commit(&bars.drain);
     volatile int never = 0;
     const long long lim = 2000000000LL;
@@ -797,7 +861,7 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (producer) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS)
+  if (warp == 4 * P) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS)
                              : "memory");
 }
 
