@@ -2,6 +2,8 @@
 // C ABI declared in include/tbbt.h. Every step of the computation runs in the
 // kernels of apply_kernels.cuh; this file only validates, allocates and
 // launches.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -117,6 +119,7 @@ struct tbbt_plan {
   int *d_sflags = nullptr;
   int64_t *d_zfix = nullptr;  // tensor-core form: fixed-point copy of the eigenvector block
   int64_t ldz = 0;
+  CUtensorMap zmap;           // tiled view of d_zfix: boxes of 16 rows x 128 columns, 128-byte swizzle
   // device copies used by the host-buffer entry points (allocated on demand)
   void *d_hv = nullptr, *d_ht = nullptr, *d_q = nullptr;
   int64_t d_q_ld = 0;
@@ -239,6 +242,22 @@ tbbt_status tc_setup_b(tbbt_plan *p) {
   }
   TBBT_CUDA_TRY(cudaMemset(p->d_zfix, 0, sizeof(int64_t) * (size_t)p->nev * (size_t)p->ldz));
   TBBT_CUDA_TRY(cudaMemcpy(p->d_block_start, start.data(), sizeof(int64_t) * start.size(), cudaMemcpyHostToDevice));
+  {
+    // the tensor map of the fixed-point block (driver entry point, no link to libcuda)
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    TBBT_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr));
+    if (qr != cudaDriverEntryPointSuccess || !fn) return TBBT_ENOTSUP;
+    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    const cuuint64_t gdim[2] = {(cuuint64_t)p->ldz, (cuuint64_t)p->nev};
+    const cuuint64_t gstride[1] = {(cuuint64_t)p->ldz * sizeof(int64_t)};
+    const cuuint32_t box[2] = {(cuuint32_t)STG_ROWS, (cuuint32_t)WS};
+    const cuuint32_t estr[2] = {1, 1};
+    if (encode(&p->zmap, CU_TENSOR_MAP_DATA_TYPE_INT64, 2, p->d_zfix, gdim, gstride, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return TBBT_ECUDA;
+  }
   TBBT_CUDA_TRY(allow_max_dynamic_smem(tc_apply_kernel<B>));
   TBBT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   TBBT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_apply_kernel<B>, D::NTHREADS, p->s_smem));
@@ -288,7 +307,7 @@ tbbt_status tc_execute(tbbt_plan *p, void *q, int64_t ldq, cudaStream_t s) {
   a.err = p->d_err;
   a.timeout_ns = p->timeout_ns;
   a.withhold = p->withhold;
-  tc_apply_kernel<B><<<(unsigned)p->s_grid, D::NTHREADS, p->s_smem, s>>>(a);
+  tc_apply_kernel<B><<<(unsigned)p->s_grid, D::NTHREADS, p->s_smem, s>>>(a, p->zmap);
   TBBT_CUDA_TRY(cudaGetLastError());
   from_fixed_kernel<<<cblocks, 256, 0, s>>>((double *)q, ldq, p->d_zfix, p->ldz, p->g.n, p->nev, p->d_colexp);
   TBBT_CUDA_TRY(cudaGetLastError());

@@ -43,6 +43,7 @@
 // Dependencies between sweeps, the work-unit queue and the bounded waits are
 // those of the FP64 kernel (one sweep of one strip per unit).
 #pragma once
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -58,7 +59,7 @@ constexpr int LV = 7;        // levels kept (0-based l = i + k <= 6)
 constexpr int WS = 128;      // strip columns = MMA M
 constexpr int FIX = 61;      // fixed-point exponent of the eigenvector block
 constexpr int FOP = 60;      // fixed-point exponent of V', U' and normalised W
-constexpr int STG_LD = 34;   // staging row stride per column (int64; 272 bytes)
+constexpr int STG_ROWS = 16;  // rows per staging box (16 x 8 bytes = one 128-byte swizzle row per column)
 constexpr int TMEM_COLS = 512;
 constexpr int REG_B = 224;   // second TMEM region (first one starts at column 0)
 
@@ -87,9 +88,9 @@ struct Geo {
   static constexpr int OFF_W = OFF_Z + 2 * ZDIG;         // S W digit buffers
   static constexpr int OFF_V = OFF_W + S * WDIG;
   static constexpr int OFF_U = OFF_V + VBYTES;
-  static constexpr int OFF_STG = OFF_U + UBYTES;
-  static constexpr int OFF_KMX = OFF_STG + WS * STG_LD * 8;  // [P][WS] partial maxima of |W|
-  static constexpr int SMEM = OFF_KMX + P * WS * 8;
+  static constexpr int OFF_STG = (OFF_U + UBYTES + 1023) / 1024 * 1024;  // two swizzled boxes [c][16 rows]
+  static constexpr int OFF_KMX = OFF_STG + 2 * WS * STG_ROWS * 8;      // [P][WS] partial maxima of |W|
+  static constexpr int SMEM = OFF_KMX + P * WS * 8 + 1024;  // + room to align the base to 1024 bytes
 };
 
 // byte offset of element (row, k) of a K-major operand with kt values of k per
@@ -171,6 +172,14 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
                    smem_u32(dst)),
                "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
+}
+// 2-D tiled TMA load (tensor map in kernel-parameter space) completing on an mbarrier
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int32_t x, int32_t y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 __device__ __forceinline__ void named_sync(int id, int count) {
@@ -439,18 +448,25 @@ struct TcArgs {
 template <int C>
 __device__ __forceinline__ void w_levels(uint32_t taddr, int64_t *w) {
 #pragma unroll
-  for (int l = 0; l < LV; ++l) {
-    uint32_t r[C];
-    if constexpr (C == 8) tmem_ld8(taddr + 32 * l, r);
-    else tmem_ld4(taddr + 32 * l, r);
+  for (int l = 0; l < LV; l += 2) {
+    uint32_t r[2][C];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      if (l + h < LV) {
+        if constexpr (C == 8) tmem_ld8(taddr + 32 * (l + h), r[h]);
+        else tmem_ld4(taddr + 32 * (l + h), r[h]);
+      }
     tc_wait_ld();
 #pragma unroll
-    for (int i = 0; i < C; ++i) {
-      const int32_t v = __float2int_rn(__uint_as_float(r[i]));  // |v| < 2^24: exact
-      if (l == 0) w[i] = v;
-      else if (l < LV - 1) w[i] = shl8_add(w[i], v);
-      else w[i] = (int64_t)((uint64_t)w[i] << 2) + (v >> 6);  // 4 h + floor(a_6 / 64)
-    }
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int i = 0; i < C; ++i) {
+        if (l + h >= LV) continue;
+        const int32_t v = __float2int_rn(__uint_as_float(r[h][i]));  // |v| < 2^24: exact
+        if (l + h == 0) w[i] = v;
+        else if (l + h < LV - 1) w[i] = shl8_add(w[i], v);
+        else w[i] = (int64_t)((uint64_t)w[i] << 2) + (v >> 6);  // 4 h + floor(a_6 / 64)
+      }
   }
 }
 
@@ -459,11 +475,13 @@ struct TcBarriers {
 };
 
 template <int B>
-__global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a) {
+__global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a, const __grid_constant__ CUtensorMap zmap) {
   using D = Geo<B>;
   constexpr int P = D::P;
   constexpr int RP = D::RP;
-  extern __shared__ __align__(1024) unsigned char smem[];
+  extern __shared__ __align__(1024) unsigned char smem_dyn[];
+  // the swizzled staging boxes need a 1024-byte aligned base
+  unsigned char *const smem = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
   __shared__ TcBarriers bars;
   __shared__ uint32_t s_tmem;
   __shared__ int s_unit;
@@ -626,11 +644,10 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a)
                 s_abort = 1;
                 break;
               }
-              const int ncols = min(WS, a.nev - c0);
-              mbar_expect_tx(&bars.stage, (uint32_t)ncols * 256u);
-              for (int c = 0; c < ncols; ++c)
-                bulk_load(smem + D::OFF_STG + c * STG_LD * 8, a.z + (int64_t)(c0 + c) * a.ldz + rn + 1, 256u,
-                          &bars.stage);
+              // two boxes of 16 rows x 128 columns (columns past nev read as zeros)
+              mbar_expect_tx(&bars.stage, 2u * WS * STG_ROWS * 8);
+              tma_load_2d(smem + D::OFF_STG, &zmap, rn + 1, c0, &bars.stage);
+              tma_load_2d(smem + D::OFF_STG + WS * STG_ROWS * 8, &zmap, rn + 1 + STG_ROWS, c0, &bars.stage);
               ++iss_st;
             }
             // U' is free once GEMM2 is done
@@ -817,13 +834,18 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a)
               for (int i = 0; i < 32; ++i)
                 if (rb + i < g.n) dst[rb + i] = z[i] - C;
             }
-            __threadfence();
-            named_sync(2 + grp, 128);
+            named_sync(2 + grp, 128);  // then one release publishes the group's stores
             if ((warp & 3) == 0 && lane == 0 && publish) st_release(myflag, rb);
             if (!mbar_wait(&bars.stage, n_st & 1, &s_abort, a.err, a.timeout_ns)) break;
-            const int64_t *stg = reinterpret_cast<const int64_t *>(smem + D::OFF_STG) + col * STG_LD;
+            // 128-byte swizzle: the 16-byte chunk j of column c sits at chunk j ^ (c mod 8)
 #pragma unroll
-            for (int i = 0; i < 32; ++i) z[i] = colok ? stg[i] + C : C;
+            for (int i2 = 0; i2 < 16; ++i2) {
+              const unsigned char *src = smem + D::OFF_STG + (i2 >> 3) * (WS * STG_ROWS * 8) + col * 128 +
+                                         (((i2 & 7) ^ (col & 7)) << 4);
+              const longlong2 v2 = *reinterpret_cast<const longlong2 *>(src);
+              z[2 * i2] = v2.x + C;
+              z[2 * i2 + 1] = v2.y + C;
+            }
           }
           if (t + 1 < nblk) ++n_st;  // every group counts every staged load
         }
@@ -836,7 +858,6 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a)
             for (int i = 0; i < 32; ++i)
               if (rb + i < g.n) dst[rb + i] = z[i] - C;
           }
-          __threadfence();
         }
       }
     }
