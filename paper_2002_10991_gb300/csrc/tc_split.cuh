@@ -610,15 +610,20 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
             ++n_u;
             if (!mbar_wait(&bars.wfull, n_blk & 1, &s_abort, a.err, a.timeout_ns)) break;
             tc_fence_after();
-            for (int p = 0; p < P && ok; ++p) {
-              if (p == 2) {
+            // parts in the order P-1 (the part leaving the window: its group then
+            // stores it and takes the new rows while the others are computed),
+            // 0, 1; part 0 in region A (free since W was read), the others in
+            // region B one after the other
+            for (int o = 0; o < P && ok; ++o) {
+              const int p = (o == 0) ? P - 1 : o - 1;
+              if (o == 2) {
                 if (!mbar_wait(&bars.cfree, n_blk & 1, &s_abort, a.err, a.timeout_ns)) {
                   ok = false;
                   break;
                 }
                 tc_fence_after();
               }
-              const uint32_t dreg = tmem + ((p & 1) ? 0u : (uint32_t)REG_B);
+              const uint32_t dreg = tmem + (p == 0 ? 0u : (uint32_t)REG_B);
               const uint32_t ub = ubase + p * D::UCHUNK;
               for (int k = 0; k < S; ++k) {
                 const int ni = (S < LV - k) ? S : LV - k;
@@ -634,24 +639,25 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
                 }
               }
               tc_commit(&bars.c[p]);
+              if (o == 0 && t + 1 < nblk) {
+                // rows of the next block's new part (the previous sweep must
+                // have finished them): two boxes of 16 rows x 128 columns
+                // (columns past nev read as zeros)
+                const int32_t rn = r0 - NB;
+                if (prevflag && wait_released_raw(a.err, a.timeout_ns, prevflag, rn)) {
+                  s_abort = 1;
+                  ok = false;
+                  break;
+                }
+                mbar_expect_tx(&bars.stage, 2u * WS * STG_ROWS * 8);
+                tma_load_2d(smem + D::OFF_STG, &zmap, rn + 1, c0, &bars.stage);
+                tma_load_2d(smem + D::OFF_STG + WS * STG_ROWS * 8, &zmap, rn + 1 + STG_ROWS, c0, &bars.stage);
+                ++iss_st;
+              }
             }
             if (!ok) break;
-            // rows of the next block's new part (the previous sweep must have
-            // finished them): one bulk copy of 32 rows per column
-            if (t + 1 < nblk) {
-              const int32_t rn = r0 - NB;
-              if (prevflag && wait_released_raw(a.err, a.timeout_ns, prevflag, rn)) {
-                s_abort = 1;
-                break;
-              }
-              // two boxes of 16 rows x 128 columns (columns past nev read as zeros)
-              mbar_expect_tx(&bars.stage, 2u * WS * STG_ROWS * 8);
-              tma_load_2d(smem + D::OFF_STG, &zmap, rn + 1, c0, &bars.stage);
-              tma_load_2d(smem + D::OFF_STG + WS * STG_ROWS * 8, &zmap, rn + 1 + STG_ROWS, c0, &bars.stage);
-              ++iss_st;
-            }
-            // U' is free once GEMM2 is done
-            if (!mbar_wait(&bars.c[P - 1], n_blk & 1, &s_abort, a.err, a.timeout_ns)) break;
+            // U' is free once GEMM2 is done (the last part issued: 1, or 0 for P = 2)
+            if (!mbar_wait(&bars.c[P == 3 ? 1 : 0], n_blk & 1, &s_abort, a.err, a.timeout_ns)) break;
             ++n_blk;
             if (t + 1 < nblk) {
               mbar_expect_tx(&bars.u, D::UBYTES);
@@ -781,7 +787,7 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
           if (!mbar_wait(&bars.c[p], n_blk & 1, &s_abort, a.err, a.timeout_ns)) break;
           tc_fence_after();
           const int rs = 50 + gv - kcol;
-          const uint32_t dreg = tmem + lane_base + ((p & 1) ? 0u : (uint32_t)REG_B);
+          const uint32_t dreg = tmem + lane_base + (p == 0 ? 0u : (uint32_t)REG_B);
 #pragma unroll
           for (int q = 0; q < 4; ++q) {  // 8 rows at a time
             int64_t t1[8], t2[8];
@@ -820,7 +826,7 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
               z[r] -= shl_signed(t1[i], sh - 24) + shl_signed(t2[i], sh - 48);
             }
           }
-          if (P == 3 && p == 0) {
+          if (P == 3 && p == P - 1) {  // region B is free for part 1
             tc_fence_before();
             mbar_arrive(&bars.cfree);
           }
