@@ -74,7 +74,10 @@ struct Geo {
   static constexpr int RP = (R + 31) / 32 * 32;  // window rows, padded
   static constexpr int P = RP / 32;              // parts of 32 rows
   static constexpr int KS1 = RP / 16;            // K steps of GEMM1
-  static constexpr int NMATH = 4 * P * 32;       // threads of the math warps
+  static constexpr int H = 2;                    // threads per column and part
+  static constexpr int RT = 32 / H;              // rows of a part held by one thread
+  static constexpr int NSUB = P * H;             // thread sets covering all 128 columns
+  static constexpr int NMATH = 4 * P * H * 32;   // threads of the math warps
   static constexpr int NTHREADS = NMATH + 32;    // + the producer warp
   static constexpr int SBO1 = (RP / 8) * 128;    // row-group stride of K = RP operands
   static constexpr int VBYTES = S * NB * RP * 2;         // V' digits [32 i + m][r]
@@ -89,8 +92,8 @@ struct Geo {
   static constexpr int OFF_V = OFF_W + S * WDIG;
   static constexpr int OFF_U = OFF_V + VBYTES;
   static constexpr int OFF_STG = (OFF_U + UBYTES + 1023) / 1024 * 1024;  // two swizzled boxes [c][16 rows]
-  static constexpr int OFF_KMX = OFF_STG + 2 * WS * STG_ROWS * 8;      // [P][WS] partial maxima of |W|
-  static constexpr int SMEM = OFF_KMX + P * WS * 8 + 1024;  // + room to align the base to 1024 bytes
+  static constexpr int OFF_KMX = OFF_STG + 2 * WS * STG_ROWS * 8;      // [NSUB][WS] partial maxima of |W|
+  static constexpr int SMEM = OFF_KMX + NSUB * WS * 8 + 1024;  // + room to align the base to 1024 bytes
 };
 
 // byte offset of element (row, k) of a K-major operand with kt values of k per
@@ -147,6 +150,12 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                : "r"(taddr)
                : "memory");
+}
+template <int C>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&r)[C]) {
+  if constexpr (C == 16) tmem_ld16(taddr, r);
+  else if constexpr (C == 8) tmem_ld8(taddr, r);
+  else tmem_ld4(taddr, r);
 }
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
@@ -249,24 +258,25 @@ __device__ __forceinline__ uint2 digits4(const int64_t *x) {
   }
   return make_uint2(w[0], w[1]);
 }
-template <int K>
-__device__ __forceinline__ void store_digits32(unsigned char *buf, int c, int rowq0, int kt, const int64_t (&z)[32]) {
-  // 32 consecutive K positions (rowq0 .. rowq0 + 31) of column c
+template <int K, int R>
+__device__ __forceinline__ void store_digits(unsigned char *buf, int c, int row0, int kt, const int64_t (&z)[R]) {
+  // R consecutive K positions (row0 .. row0 + R - 1) of column c
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < R / 8; ++q) {
     const uint4 v = digits8<K>(z + 8 * q);
-    *reinterpret_cast<uint4 *>(buf + kmaj(c, rowq0 + 8 * q, kt)) = v;
+    *reinterpret_cast<uint4 *>(buf + kmaj(c, row0 + 8 * q, kt)) = v;
   }
 }
-__device__ __forceinline__ void store_z_digit(int k, unsigned char *buf, int c, int rowq0, int kt,
-                                              const int64_t (&z)[32]) {
+template <int R>
+__device__ __forceinline__ void store_z_digit(int k, unsigned char *buf, int c, int row0, int kt,
+                                              const int64_t (&z)[R]) {
   switch (k) {
-    case 1: store_digits32<1>(buf, c, rowq0, kt, z); break;
-    case 2: store_digits32<2>(buf, c, rowq0, kt, z); break;
-    case 3: store_digits32<3>(buf, c, rowq0, kt, z); break;
-    case 4: store_digits32<4>(buf, c, rowq0, kt, z); break;
-    case 5: store_digits32<5>(buf, c, rowq0, kt, z); break;
-    default: store_digits32<6>(buf, c, rowq0, kt, z); break;
+    case 1: store_digits<1, R>(buf, c, row0, kt, z); break;
+    case 2: store_digits<2, R>(buf, c, row0, kt, z); break;
+    case 3: store_digits<3, R>(buf, c, row0, kt, z); break;
+    case 4: store_digits<4, R>(buf, c, row0, kt, z); break;
+    case 5: store_digits<5, R>(buf, c, row0, kt, z); break;
+    default: store_digits<6, R>(buf, c, row0, kt, z); break;
   }
 }
 
@@ -489,13 +499,14 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
   __shared__ volatile int s_abort;
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  const bool producer = warp == 4 * P;
-  const int grp = warp >> 2;                // math group (parts rotate over groups)
+  const bool producer = warp == 4 * P * D::H;
+  const int grp = warp / (4 * D::H);        // math group (parts rotate over groups)
+  const int hf = (warp >> 2) % D::H;        // which rows of the part: RT * hf ..
   const int col = (warp & 3) * 32 + lane;   // strip column of this math thread = its TMEM lane
   const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
   const StoreGeom &g = a.g;
 
-  if (warp == 4 * P) {
+  if (warp == 4 * P * D::H) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_tmem)),
                  "r"(TMEM_COLS)
                  : "memory");
@@ -509,7 +520,7 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
     mbar_init(&bars.g1, 1);
     mbar_init(&bars.wfull, D::NMATH);
     for (int p = 0; p < 3; ++p) mbar_init(&bars.c[p], 1);
-    mbar_init(&bars.cfree, 128);
+    mbar_init(&bars.cfree, 128 * D::H);
     mbar_init(&bars.v, 1);
     mbar_init(&bars.u, 1);
     mbar_init(&bars.stage, 1);
@@ -555,7 +566,7 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
 
     if (!s_abort) {
       if (producer) {
-        if (warp == 4 * P && lane == 0) {
+        if (warp == 4 * P * D::H && lane == 0) {
           // ------------------------------------------------------------ producer
           const unsigned char *blkp = a.slices + blk0 * (int64_t)D::BLOCK_BYTES;
           mbar_expect_tx(&bars.v, D::VBYTES);
@@ -669,31 +680,62 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
         __syncwarp();
       } else {
         // -------------------------------------------------------------- math
+        constexpr int RT = D::RT;
         const int64_t C = kDigitOffset;
         const bool colok = c0 + col < a.nev;
         const int64_t *zcol = a.z + (int64_t)(c0 + col) * a.ldz + 1;
-        int64_t z[32];  // my part of the window, offset form
+        int64_t z[RT];  // rows RT * hf .. of my part of the window, offset form
         {
-          const int32_t rb = r0_of(0) + 32 * grp;
+          const int32_t rb = r0_of(0) + 32 * grp + RT * hf;
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
+          for (int i = 0; i < RT; ++i) {
             const int32_t r = rb + i;
             z[i] = (colok && r < g.n) ? (int64_t)__ldcg((const long long *)(zcol + r)) + C : C;
           }
         }
+        // reflector range of this thread set in the W readout
+        const int sub = D::H * grp + hf;
+        int ca0, cw0, ca1, cw1;
+        if (D::NSUB == 6) {  // 8 / 4 / 4 / 4 / 4 / 8
+          ca0 = sub == 0 ? 0 : (sub == 5 ? 24 : 4 + 4 * sub);
+          cw0 = (sub == 0 || sub == 5) ? 8 : 4;
+          ca1 = 0;
+          cw1 = 0;
+        } else if (D::NSUB == 4) {  // 8 each
+          ca0 = 8 * sub;
+          cw0 = 8;
+          ca1 = 0;
+          cw1 = 0;
+        } else if (D::NSUB == 3) {  // 12 / 12 / 8
+          ca0 = sub == 0 ? 0 : (sub == 1 ? 12 : 24);
+          cw0 = sub == 1 ? 4 : 8;
+          ca1 = sub == 0 ? 8 : 16;
+          cw1 = sub == 0 ? 4 : (sub == 1 ? 8 : 0);
+        } else {  // 16 / 16
+          ca0 = 16 * sub;
+          cw0 = 8;
+          ca1 = 16 * sub + 8;
+          cw1 = 8;
+        }
         for (int32_t t = 0; t < nblk; ++t) {
           const int32_t r0 = r0_of(t);
           const int p = (grp + t) % P;  // my part of this block's window
+          const int prow = 32 * p + RT * hf;  // my first window row
           const int64_t blk = blk0 + t;
-          // per-row exponents of U for my part, and the block's V scale (read now, used late)
-          uint32_t gu4[8];
+          // per-row exponents of U for my rows, and the block's V scale (read now, used late)
+          uint32_t gu4[RT / 4];
           int gv;
           {
             const uint4 *gsrc = reinterpret_cast<const uint4 *>(a.slices + blk * (int64_t)D::BLOCK_BYTES + D::VBYTES +
-                                                                D::UBYTES + 32 * p);
-            const uint4 g0 = __ldg(gsrc), g1 = __ldg(gsrc + 1);
-            gu4[0] = g0.x; gu4[1] = g0.y; gu4[2] = g0.z; gu4[3] = g0.w;
-            gu4[4] = g1.x; gu4[5] = g1.y; gu4[6] = g1.z; gu4[7] = g1.w;
+                                                                D::UBYTES + prow);
+#pragma unroll
+            for (int i = 0; i < RT / 16; ++i) {
+              const uint4 gq = __ldg(gsrc + i);
+              gu4[4 * i] = gq.x;
+              gu4[4 * i + 1] = gq.y;
+              gu4[4 * i + 2] = gq.z;
+              gu4[4 * i + 3] = gq.w;
+            }
             gv = __ldg(a.gvs + blk);
           }
           // ---- digits of Z -> GEMM1
@@ -705,7 +747,7 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
               ok = false;
               break;
             }
-            store_z_digit(k, smem + D::OFF_Z + zb * D::ZDIG, col, 32 * p, RP, z);
+            store_z_digit<RT>(k, smem + D::OFF_Z + zb * D::ZDIG, col, prow, RP, z);
             fence_proxy_async();
             tc_fence_before();
             mbar_arrive(&bars.zfull[zb]);
@@ -715,19 +757,6 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
           // ---- W = V'^T Z for my column and my reflector range
           if (!mbar_wait(&bars.g1, n_blk & 1, &s_abort, a.err, a.timeout_ns)) break;
           tc_fence_after();
-          // reflector chunks of this group: 12 / 12 / 8 (b = 64) or 16 / 16 (b = 32)
-          int ca0, cw0, ca1, cw1;
-          if (P == 3) {
-            ca0 = grp == 0 ? 0 : (grp == 1 ? 12 : 24);
-            cw0 = grp == 1 ? 4 : 8;
-            ca1 = grp == 0 ? 8 : 16;
-            cw1 = grp == 0 ? 4 : (grp == 1 ? 8 : 0);
-          } else {
-            ca0 = 16 * grp;
-            cw0 = 8;
-            ca1 = 16 * grp + 8;
-            cw1 = 8;
-          }
           int64_t w[16];
           const uint32_t wt = tmem + lane_base;
           if (cw0 == 8) w_levels<8>(wt + ca0, w);
@@ -743,23 +772,23 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
             }
           }
           uint64_t *kmx = reinterpret_cast<uint64_t *>(smem + D::OFF_KMX);
-          kmx[grp * WS + col] = mx;
+          kmx[sub * WS + col] = mx;
           named_sync(1, D::NMATH);
 #pragma unroll
-          for (int q = 0; q < P; ++q) {
+          for (int q = 0; q < D::NSUB; ++q) {
             const uint64_t o = kmx[q * WS + col];
             mx = o > mx ? o : mx;
           }
           const int bits = mx ? 64 - __clzll((long long)mx) : 0;
           const int kcol = (bits > 0 && bits < FOP) ? FOP - bits : 0;
-#pragma unroll
-          for (int i = 0; i < 16; ++i) w[i] = (int64_t)((uint64_t)w[i] << kcol) + C;
           {
             unsigned char *wb = smem + D::OFF_W;
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
               const int cw = q ? cw1 : cw0;
-              const int64_t *wq = w + 8 * q;
+              int64_t *wq = w + 8 * q;
+#pragma unroll
+              for (int i = 0; i < 8; ++i) wq[i] = (int64_t)((uint64_t)wq[i] << kcol) + C;
               const int koff = kmaj(col, q ? ca1 : ca0, NB);
               if (cw == 8) {
                 *reinterpret_cast<uint4 *>(wb + 0 * D::WDIG + koff) = digits8<1>(wq);
@@ -781,47 +810,48 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
           fence_proxy_async();
           tc_fence_before();
           mbar_arrive(&bars.wfull);
-          // ---- corr of my part: Z -= sum_l B_l 2^(rs + gu[r] - 8 l); levels in
+          // ---- corr of my rows: Z -= sum_l B_l 2^(rs + gu[r] - 8 l); levels in
           // pairs (a_l 2^8 + a_(l+1) is exact in 32 bits, |a| < 2^22), then
           // T = P01 2^16 + P23 and T2 = P45 2^8 + a_6 (exact in 64 bits)
           if (!mbar_wait(&bars.c[p], n_blk & 1, &s_abort, a.err, a.timeout_ns)) break;
           tc_fence_after();
           const int rs = 50 + gv - kcol;
-          const uint32_t dreg = tmem + lane_base + (p == 0 ? 0u : (uint32_t)REG_B);
+          const uint32_t dreg = tmem + lane_base + (p == 0 ? 0u : (uint32_t)REG_B) + RT * hf;
+          constexpr int PR = (RT >= 16) ? 4 : 8;  // rows per piece (register budget)
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {  // 8 rows at a time
-            int64_t t1[8], t2[8];
+          for (int q = 0; q < RT / PR; ++q) {
+            int64_t t1[PR], t2[PR];
             {
-              uint32_t ra[8], rb[8];
-              int32_t p01[8];
-              tmem_ld8(dreg + 8 * q, ra);
-              tmem_ld8(dreg + 32 + 8 * q, rb);
+              uint32_t ra[PR], rb[PR];
+              int32_t p01[PR];
+              tmem_ld<PR>(dreg + PR * q, ra);
+              tmem_ld<PR>(dreg + 32 + PR * q, rb);
               tc_wait_ld();
 #pragma unroll
-              for (int i = 0; i < 8; ++i)
+              for (int i = 0; i < PR; ++i)
                 p01[i] = f2i_small(__uint_as_float(ra[i])) * 256 + f2i_small(__uint_as_float(rb[i]));
-              tmem_ld8(dreg + 64 + 8 * q, ra);
-              tmem_ld8(dreg + 96 + 8 * q, rb);
+              tmem_ld<PR>(dreg + 64 + PR * q, ra);
+              tmem_ld<PR>(dreg + 96 + PR * q, rb);
               tc_wait_ld();
 #pragma unroll
-              for (int i = 0; i < 8; ++i)
+              for (int i = 0; i < PR; ++i)
                 t1[i] = (int64_t)((uint64_t)(int64_t)p01[i] << 16) +
                         (f2i_small(__uint_as_float(ra[i])) * 256 + f2i_small(__uint_as_float(rb[i])));
-              tmem_ld8(dreg + 128 + 8 * q, ra);
-              tmem_ld8(dreg + 160 + 8 * q, rb);
+              tmem_ld<PR>(dreg + 128 + PR * q, ra);
+              tmem_ld<PR>(dreg + 160 + PR * q, rb);
               tc_wait_ld();
 #pragma unroll
-              for (int i = 0; i < 8; ++i)
+              for (int i = 0; i < PR; ++i)
                 p01[i] = f2i_small(__uint_as_float(ra[i])) * 256 + f2i_small(__uint_as_float(rb[i]));
-              tmem_ld8(dreg + 192 + 8 * q, ra);
+              tmem_ld<PR>(dreg + 192 + PR * q, ra);
               tc_wait_ld();
 #pragma unroll
-              for (int i = 0; i < 8; ++i)
+              for (int i = 0; i < PR; ++i)
                 t2[i] = (int64_t)((uint64_t)(int64_t)p01[i] << 8) + f2i_small(__uint_as_float(ra[i]));
             }
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const int r = 8 * q + i;
+            for (int i = 0; i < PR; ++i) {
+              const int r = PR * q + i;
               const int sh = rs + (int)(int8_t)(gu4[r >> 2] >> (8 * (r & 3)));
               z[r] -= shl_signed(t1[i], sh - 24) + shl_signed(t2[i], sh - 48);
             }
@@ -833,21 +863,22 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
           ++n_blk;
           // ---- the part leaving the window: store it, take the new rows
           if (t + 1 < nblk && p == P - 1) {
-            const int32_t rb = r0 + 32 * (P - 1);
+            const int32_t rb = r0 + 32 * (P - 1) + RT * hf;
             if (colok) {
               int64_t *dst = a.z + (int64_t)(c0 + col) * a.ldz + 1;
 #pragma unroll
-              for (int i = 0; i < 32; ++i)
+              for (int i = 0; i < RT; ++i)
                 if (rb + i < g.n) dst[rb + i] = z[i] - C;
             }
-            named_sync(2 + grp, 128);  // then one release publishes the group's stores
-            if ((warp & 3) == 0 && lane == 0 && publish) st_release(myflag, rb);
+            named_sync(2 + grp, 128 * D::H);  // then one release publishes the group's stores
+            if ((warp & 3) == 0 && hf == 0 && lane == 0 && publish) st_release(myflag, rb);
             if (!mbar_wait(&bars.stage, n_st & 1, &s_abort, a.err, a.timeout_ns)) break;
             // 128-byte swizzle: the 16-byte chunk j of column c sits at chunk j ^ (c mod 8)
 #pragma unroll
-            for (int i2 = 0; i2 < 16; ++i2) {
-              const unsigned char *src = smem + D::OFF_STG + (i2 >> 3) * (WS * STG_ROWS * 8) + col * 128 +
-                                         (((i2 & 7) ^ (col & 7)) << 4);
+            for (int i2 = 0; i2 < RT / 2; ++i2) {
+              const int r = RT * hf + 2 * i2;  // row within the new part (pairs)
+              const unsigned char *src = smem + D::OFF_STG + (r >> 4) * (WS * STG_ROWS * 8) + col * 128 +
+                                         ((((r & 15) >> 1) ^ (col & 7)) << 4);
               const longlong2 v2 = *reinterpret_cast<const longlong2 *>(src);
               z[2 * i2] = v2.x + C;
               z[2 * i2 + 1] = v2.y + C;
@@ -857,11 +888,11 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
         }
         if (!s_abort) {
           // the whole last window is final
-          const int32_t rb = r0_of(nblk - 1) + 32 * ((grp + nblk - 1) % P);
+          const int32_t rb = r0_of(nblk - 1) + 32 * ((grp + nblk - 1) % P) + RT * hf;
           if (colok) {
             int64_t *dst = a.z + (int64_t)(c0 + col) * a.ldz + 1;
 #pragma unroll
-            for (int i = 0; i < 32; ++i)
+            for (int i = 0; i < RT; ++i)
               if (rb + i < g.n) dst[rb + i] = z[i] - C;
           }
         }
@@ -874,7 +905,7 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
     if (tid == 0 && publish) st_release(myflag, r0_of(nblk - 1));
   }
   // drain: no copy or MMA of this block may still be in flight at exit
-  if (s_abort && warp == 4 * P && lane == 0) {
+  if (s_abort && warp == 4 * P * D::H && lane == 0) {
     tc_commit(&bars.drain);
     volatile int never = 0;
     const long long lim = 2000000000LL;
@@ -888,7 +919,7 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 4 * P) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS)
+  if (warp == 4 * P * D::H) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS)
                              : "memory");
 }
 
