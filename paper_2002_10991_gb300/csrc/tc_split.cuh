@@ -287,6 +287,27 @@ __device__ __forceinline__ int64_t shl_signed(int64_t x, int s) {
 }
 __device__ __forceinline__ int64_t shl8_add(int64_t h, int32_t v) { return (int64_t)((uint64_t)h << 8) + v; }
 
+// round(x * 2^sh) for |x * 2^sh| < 2^62, from the bits of x (integer unit only;
+// halves round up); zero and subnormal x give 0
+__device__ __forceinline__ int64_t fix_round(double x, int sh) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e == 0) return 0;
+  const uint64_t mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);  // |x| = mant 2^(e - 1075)
+  const int s = e - 1075 + sh;
+  int64_t r;
+  if (s >= 0) r = (int64_t)(mant << s);
+  else if (s > -64) r = (int64_t)((mant + (1ull << (-s - 1))) >> (-s));
+  else r = 0;
+  return (b >> 63) ? -r : r;
+}
+// e with |x| < 2^e (the frexp exponent) of the largest magnitude whose
+// bits (sign cleared) are m; 0 for m = 0
+__device__ __forceinline__ int exp_of_bits(uint64_t m) { return m ? (int)(m >> 52) - 1022 : 0; }
+__device__ __forceinline__ uint64_t abs_bits(double x) {
+  return (uint64_t)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
 // ---------------------------------------------------------------------------
 // per-plan preparation: FP64 T and U = V T per block, digits in the operand
 // layouts of the tensor-core kernel
@@ -302,9 +323,9 @@ __global__ void __launch_bounds__(128) tc_prepare_kernel(const double *__restric
   constexpr int RP = D::RP;
   __shared__ double sV[RP][NB + 1];  // V, later U = V T
   __shared__ double sT[NB][NB + 1];
-  __shared__ double sy[NB];
+  __shared__ double sG[NB][NB + 1];  // Gram matrix V^T V (strict upper triangle)
   __shared__ double stau[NB];
-  __shared__ double sred[4];
+  __shared__ uint64_t sred[4];
   __shared__ int sgu[RP];
   const int64_t blk = blockIdx.x;
   if (blk >= nblocks) return;
@@ -321,7 +342,7 @@ __global__ void __launch_bounds__(128) tc_prepare_kernel(const double *__restric
   const int tid = threadIdx.x;
   const int64_t base = g.sweep_offset(j) + g.imax(j);  // entry of stage s: base - s
   for (int idx = tid; idx < RP * NB; idx += blockDim.x) {
-    const int r = idx / NB, m = idx - r * NB;
+    const int m = idx / RP, r = idx - m * RP;  // consecutive threads read one entry's consecutive elements
     double val = 0.0;
     if (m < cnt) {
       const int32_t s = s_lo + m;
@@ -336,67 +357,122 @@ __global__ void __launch_bounds__(128) tc_prepare_kernel(const double *__restric
   for (int idx = tid; idx < NB * NB; idx += blockDim.x) sT[idx / NB][idx % NB] = 0.0;
   __syncthreads();
   // compact WY of H_0 H_1 ... H_{cnt-1} (H_m of stage s_lo + m; the highest
-  // stage acts first): T_mm = tau_m, T[0:m, m] = -tau_m T[0:m, 0:m] (V^T v_m)
+  // stage acts first): T_mm = tau_m, T[0:m, m] = -tau_m T[0:m, 0:m] (V^T v_m).
+  // Column k of V is zero outside rows k .. k + B - 1, so V^T v_m needs rows
+  // m .. k + B - 1 only; all of V^T V first (in parallel), then the recurrence.
+  for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
+    const int k = idx / NB, m = idx - k * NB;
+    if (k < m && m < cnt) {
+      double acc = 0.0;
+      const int rend = min(k + B, RP);
+      for (int r = m; r < rend; ++r) acc = fma(sV[r][k], sV[r][m], acc);
+      sG[k][m] = acc;
+    }
+  }
+  __syncthreads();
   for (int m = 0; m < cnt; ++m) {
     for (int k = tid; k < m; k += blockDim.x) {
       double acc = 0.0;
-      for (int r = 0; r < RP; ++r) acc += sV[r][k] * sV[r][m];
-      sy[k] = acc;
-    }
-    __syncthreads();
-    for (int k = tid; k < m; k += blockDim.x) {
-      double acc = 0.0;
-      for (int l = k; l < m; ++l) acc += sT[k][l] * sy[l];
+      for (int l = k; l < m; ++l) acc = fma(sT[k][l], sG[l][m], acc);
       sT[k][m] = -stau[m] * acc;
     }
     if (tid == 0) sT[m][m] = stau[m];
     __syncthreads();
   }
   unsigned char *out = slices + blk * (int64_t)D::BLOCK_BYTES;
-  // V' = V 2^(60 - gv), |V| <= 2^gv
-  double mx = 0.0;
-  for (int idx = tid; idx < RP * NB; idx += blockDim.x) mx = fmax(mx, fabs(sV[idx / NB][idx % NB]));
-  for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  // V' = V 2^(60 - gv), |V| <= 2^gv (magnitudes compared as IEEE bit patterns)
+  uint64_t mx = 0;
+  for (int idx = tid; idx < RP * NB; idx += blockDim.x) {
+    const uint64_t a = abs_bits(sV[idx / NB][idx % NB]);
+    mx = a > mx ? a : mx;
+  }
+  for (int o = 16; o; o >>= 1) {
+    const uint64_t a = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = a > mx ? a : mx;
+  }
   if ((tid & 31) == 0) sred[tid >> 5] = mx;
   __syncthreads();
-  mx = fmax(fmax(sred[0], sred[1]), fmax(sred[2], sred[3]));
-  int gv = 0;
-  if (mx > 0.0) frexp(mx, &gv);
-  for (int idx = tid; idx < RP * NB; idx += blockDim.x) {
-    const int m = idx / RP, r = idx - m * RP;
-    int64_t x = __double2ll_rn(ldexp(sV[r][m], FOP - gv));
-    for (int sl = 1; sl <= S; ++sl)
-      *reinterpret_cast<__nv_bfloat16 *>(out + kmaj(NB * (sl - 1) + m, r, RP)) =
-          __float2bfloat16_rn((float)split::peel_digit(x, sl));
+  mx = sred[0] > sred[1] ? sred[0] : sred[1];
+  mx = sred[2] > mx ? sred[2] : mx;
+  mx = sred[3] > mx ? sred[3] : mx;
+  const int gv = exp_of_bits(mx);
+  // each item: 8 consecutive rows of one column of V', one 16-byte chunk per digit
+  for (int idx = tid; idx < NB * (RP / 8); idx += blockDim.x) {
+    const int m = idx % NB, r0 = 8 * (idx / NB);
+    int64_t x[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) x[e] = fix_round(sV[r0 + e][m], FOP - gv);
+#pragma unroll
+    for (int sl = 1; sl <= S; ++sl) {
+      uint32_t wv[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn((float)split::peel_digit(x[2 * e], sl),
+                                                         (float)split::peel_digit(x[2 * e + 1], sl));
+        wv[e] = *reinterpret_cast<const uint32_t *>(&h2);
+      }
+      *reinterpret_cast<uint4 *>(out + kmaj(NB * (sl - 1) + m, r0, RP)) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+    }
   }
   __syncthreads();
-  // U = V T in place (column m needs V[r][0..m]: go from the last column down)
-  for (int r = tid; r < RP; r += blockDim.x)
-    for (int m = NB - 1; m >= 0; --m) {
+  // U = V T: row r of V is zero outside columns r - B + 1 .. r; each thread
+  // computes its outputs in registers, then all write them over V
+  {
+    constexpr int PER = RP * NB / 128;  // outputs per thread (128 threads)
+    double u[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int idx = tid + 128 * i;
+      const int r = idx / NB, m = idx - r * NB;
       double acc = 0.0;
-      for (int k = 0; k <= m; ++k) acc += sV[r][k] * sT[k][m];
-      sV[r][m] = acc;
+      const int k0 = max(0, r - B + 1), k1 = min(m, r);
+      for (int k = k0; k <= k1; ++k) acc = fma(sV[r][k], sT[k][m], acc);
+      u[i] = acc;
     }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int idx = tid + 128 * i;
+      sV[idx / NB][idx % NB] = u[i];
+    }
+  }
   __syncthreads();
   // U' = U 2^(60 - gu[r]) per row, |U[r][:]| <= 2^gu[r]
   int8_t *rowexp = reinterpret_cast<int8_t *>(out + D::VBYTES + D::UBYTES);
   for (int r = tid; r < RP; r += blockDim.x) {
-    double m2 = 0.0;
-    for (int m = 0; m < NB; ++m) m2 = fmax(m2, fabs(sV[r][m]));
-    int e = 0;
-    if (m2 > 0.0) frexp(m2, &e);
+    uint64_t m2 = 0;
+    for (int m = 0; m < NB; ++m) {
+      const uint64_t a = abs_bits(sV[r][m]);
+      m2 = a > m2 ? a : m2;
+    }
+    // rows below 2^-64 keep the scale of 2^-64 (their contribution is far
+    // below the digit truncation); the exponent fits int8
+    int e = exp_of_bits(m2);
+    e = e < -64 ? -64 : (e > 100 ? 100 : e);
     sgu[r] = e;
     rowexp[r] = (int8_t)e;
   }
   for (int r = RP + tid; r < D::EBYTES; r += blockDim.x) rowexp[r] = 0;
   __syncthreads();
-  for (int idx = tid; idx < RP * NB; idx += blockDim.x) {
-    const int r = idx / NB, m = idx - r * NB;
+  // each item: 8 consecutive columns of one row of U', one 16-byte chunk per digit
+  for (int idx = tid; idx < RP * (NB / 8); idx += blockDim.x) {
+    const int r = idx % RP, m0 = 8 * (idx / RP);
     const int part = r >> 5, rr = r & 31;
-    int64_t x = __double2ll_rn(ldexp(sV[r][m], FOP - sgu[r]));
-    for (int sl = 1; sl <= S; ++sl)
-      *reinterpret_cast<__nv_bfloat16 *>(out + D::VBYTES + part * D::UCHUNK + kmaj(NB * (sl - 1) + rr, m, NB)) =
-          __float2bfloat16_rn((float)split::peel_digit(x, sl));
+    int64_t x[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) x[e] = fix_round(sV[r][m0 + e], FOP - sgu[r]);
+#pragma unroll
+    for (int sl = 1; sl <= S; ++sl) {
+      uint32_t wv[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn((float)split::peel_digit(x[2 * e], sl),
+                                                         (float)split::peel_digit(x[2 * e + 1], sl));
+        wv[e] = *reinterpret_cast<const uint32_t *>(&h2);
+      }
+      *reinterpret_cast<uint4 *>(out + D::VBYTES + part * D::UCHUNK + kmaj(NB * (sl - 1) + rr, m0, NB)) =
+          make_uint4(wv[0], wv[1], wv[2], wv[3]);
+    }
   }
   if (tid == 0) gvs[blk] = gv;
 }
@@ -757,15 +833,18 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
           // ---- W = V'^T Z for my column and my reflector range
           if (!mbar_wait(&bars.g1, n_blk & 1, &s_abort, a.err, a.timeout_ns)) break;
           tc_fence_after();
-          int64_t w[16];
+          constexpr int NW = (D::H == 2) ? 8 : 16;  // W values this thread may hold
+          int64_t w[NW];
           const uint32_t wt = tmem + lane_base;
           if (cw0 == 8) w_levels<8>(wt + ca0, w);
           else w_levels<4>(wt + ca0, w);
-          if (cw1 == 8) w_levels<8>(wt + ca1, w + 8);
-          else if (cw1 == 4) w_levels<4>(wt + ca1, w + 8);
+          if constexpr (NW == 16) {
+            if (cw1 == 8) w_levels<8>(wt + ca1, w + 8);
+            else if (cw1 == 4) w_levels<4>(wt + ca1, w + 8);
+          }
           uint64_t mx = 0;
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
+          for (int i = 0; i < NW; ++i) {
             if ((i < 8 && i < cw0) || (i >= 8 && i - 8 < cw1)) {
               const uint64_t ax = (uint64_t)(w[i] < 0 ? -w[i] : w[i]);
               mx = ax > mx ? ax : mx;
@@ -784,7 +863,7 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
           {
             unsigned char *wb = smem + D::OFF_W;
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
+            for (int q = 0; q < NW / 8; ++q) {
               const int cw = q ? cw1 : cw0;
               int64_t *wq = w + 8 * q;
 #pragma unroll
