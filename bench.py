@@ -352,6 +352,9 @@ def main():
     ap.add_argument("--ref-cols", type=int, default=256, help="columns per step of the reference arm")
     ap.add_argument("--warmup-ref", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--split-steps", type=int, default=5,
+                    help="fp64 runs of real b=32/64 workloads: also time this many steps of the tcgen05 "
+                         "split-precision form on the same inputs (0: skip)")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="named workload (default: the benchmark workload; others are for profiler captures "
                          "and the batched-form measurement)")
@@ -445,6 +448,32 @@ def main():
     ms_per_step = total_ms / args.steps
     value = flops * args.steps * world / (total_ms * 1e-3) / 1e12
 
+    # the mixed-precision form on the same inputs (headline: speedup over FP64 at the set accuracy)
+    split_tc = None
+    if not split and not cplx and b in (32, 64) and args.split_steps > 0:
+        sp = P.Plan(cplx, n, b, nev, variant=VARIANTS["split-tc"])
+        qs = torch.from_numpy(X.T.copy()).cuda().t()
+        sp.set_reflectors(dv, dt)
+        sp.execute(qs)
+        P.stream_check()
+        split_cols = qs[:, torch.from_numpy(cols).cuda()].cpu().numpy()
+        for _ in range(2):
+            sp.set_reflectors(dv, dt)
+            sp.execute(qs)
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(args.split_steps):
+            sp.set_reflectors(dv, dt)
+            sp.execute(qs)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        P.stream_check()
+        split_tc = {"ms_per_step": s0.elapsed_time(s1) / args.split_steps, "steps": args.split_steps,
+                    "cols": split_cols}
+        sp.close()
+        del qs
+
     fp64_cmp = None
     if split:
         ref = P.Plan(cplx, n, b, nev)
@@ -530,6 +559,16 @@ def main():
         }
         if fp64_cmp:
             line.update(fp64_cmp)
+        if split_tc:
+            sms = split_tc["ms_per_step"]
+            line["split_tc"] = {
+                "variant": "split_bf16_tc", "kernel": f"tbbt::tcs::tc_apply_kernel<{b}>",
+                "ms_per_step": sms, "steps": split_tc["steps"], "speedup_vs_fp64": ms_per_step / sms,
+                "fp64_equivalent_tflops": flops / (sms * 1e-3) / 1e12,
+                "tensor_tflops": tc_tensor_flops(w) / (sms * 1e-3) / 1e12,
+                "max_abs_err_vs_oracle": float(np.abs(Zo - split_tc["cols"]).max()),
+                "err_sample": cpu["sample"],
+            }
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:
