@@ -290,7 +290,7 @@ __device__ __forceinline__ void store_rows(const ApplyArgs &a, const T *ring, in
 // (read-only data: asynchronous copies, completed by wait_all + barrier).
 template <typename T>
 __device__ __forceinline__ void load_reflectors(const ApplyArgs &a, const Epoch &ep, T *vbuf_w, int32_t w,
-                                                int32_t t, int lane) {
+                                                int32_t t, int li, int nl) {
   int32_t hi, lo;
   warp_stages(a.g, ep, w, t, &hi, &lo);
   if (hi < lo) return;
@@ -301,7 +301,7 @@ __device__ __forceinline__ void load_reflectors(const ApplyArgs &a, const Epoch 
   const int32_t nchunks = (hi - lo + 1) * a.ldv * (int32_t)sizeof(T) / 16;
   const char *s8 = reinterpret_cast<const char *>(src);
   char *d8 = reinterpret_cast<char *>(dst);
-  for (int32_t c = lane; c < nchunks; c += 32) cp_async<16>(d8 + 16 * c, s8 + 16 * c);
+  for (int32_t c = li; c < nchunks; c += nl) cp_async<16>(d8 + 16 * c, s8 + 16 * c);
 }
 
 // Eq. 8 for one reflector on one column: x[r:r+L] -= tau * v * (v^H x[r:r+L]).
@@ -331,6 +331,51 @@ __device__ __forceinline__ void apply_one(T *col, int32_t ring, int32_t r, int32
       col[(int64_t)sl * 32] = x;
     }
   }
+}
+
+// Eq. 8 for one reflector on one complex column, by a pair of lanes: lane h
+// of the pair takes the rows [h ? Lh : 0, h ? L : Lh) of the window (Lh =
+// ceil(L / 2)), and the two partial sums of v^H x are added with one exchange
+// inside the pair (both lanes form the same sum: addition commutes). Each
+// lane's dependent chain is half as long, and a 32-column strip takes two
+// warps per sweep, two per SM sub-partition.
+__device__ __forceinline__ void apply_pair(zdouble *col, int32_t ring, int32_t r, int32_t L, const zdouble *ent,
+                                           int h) {
+  const int32_t Lh = (L + 1) >> 1;
+  const int32_t t0 = h ? Lh : 1, t1 = h ? L : Lh;
+  const int32_t base = r % ring;
+  zdouble s = h ? zdouble{0.0, 0.0} : col[(int64_t)base * 32];
+  int32_t sl0 = base + t0;
+  if (sl0 >= ring) sl0 -= ring;
+  {
+    int32_t sl = sl0;
+#pragma unroll 4
+    for (int32_t t = t0; t < t1; ++t) {
+      Arith<zdouble>::dot(s, ent[t], col[(int64_t)sl * 32]);
+      sl = (sl + 1 == ring) ? 0 : sl + 1;
+    }
+  }
+  s.re += __shfl_xor_sync(0xffffffffu, s.re, 1);
+  s.im += __shfl_xor_sync(0xffffffffu, s.im, 1);
+  const zdouble u = Arith<zdouble>::scale(ent[0], s);
+  if (!h) {
+    zdouble x0 = col[(int64_t)base * 32];
+    Arith<zdouble>::sub(x0, u);
+    col[(int64_t)base * 32] = x0;
+  }
+  {
+    int32_t sl = sl0;
+#pragma unroll 4
+    for (int32_t t = t0; t < t1; ++t) {
+      zdouble x = col[(int64_t)sl * 32];
+      Arith<zdouble>::axpy(x, u, ent[t]);
+      col[(int64_t)sl * 32] = x;
+      sl = (sl + 1 == ring) ? 0 : sl + 1;
+    }
+  }
+  // the next reflector starts one row up: its upper lane reads a row this
+  // reflector's lower lane just wrote
+  __syncwarp();
 }
 
 // Register-window variant of the stage loop for real data and b = B (32 or
@@ -422,10 +467,14 @@ __device__ __forceinline__ bool process_unit(const ApplyArgs &a, int32_t e, int3
   T *ring = reinterpret_cast<T *>(smem_raw);
   T *vbuf = ring + (int64_t)a.ring * 32;
   const int lane = threadIdx.x & 31;
-  const int w = threadIdx.x >> 5;
+  // BW < 0 (complex): two warps per sweep; warp half cs of the pair takes
+  // columns 16 cs .. 16 cs + 15, a lane pair per column
+  const int w = BW < 0 ? (threadIdx.x >> 6) : (threadIdx.x >> 5);
+  const int cs = (threadIdx.x >> 5) & 1;
+  const int li = BW < 0 ? lane + 32 * cs : lane, nl = BW < 0 ? 64 : 32;
   const StoreGeom &g = a.g;
   T *vbuf_w = vbuf + (int64_t)w * 2 * a.NB * a.ldv;
-  T *mycol = ring + lane;
+  T *mycol = BW < 0 ? ring + 16 * cs + (lane >> 1) : ring + lane;
   double xw[BW > 0 ? BW : 1];  // register window of the lane's column (BW > 0)
   (void)xw;
   const Epoch ep = make_epoch(g, e, a.G, a.NB);
@@ -437,7 +486,7 @@ __device__ __forceinline__ bool process_unit(const ApplyArgs &a, int32_t e, int3
   bool abandoned = *s_stop != 0;
   if (!abandoned) {
     load_rows_now<T>(a, ring, top, g.n, c0);
-    load_reflectors<T>(a, ep, vbuf_w, w, 0, lane);
+    load_reflectors<T>(a, ep, vbuf_w, w, 0, li, nl);
     cp_async_wait_all();
     __syncthreads();
     int32_t released = g.n;  // rows >= released are back in global memory
@@ -460,7 +509,7 @@ __device__ __forceinline__ bool process_unit(const ApplyArgs &a, int32_t e, int3
       }
       if (threadIdx.x == 0 && publish) st_release(myflag, released);
       pf.issue(a, ntop, top, c0);
-      load_reflectors<T>(a, ep, vbuf_w, w, t + 1, lane);
+      load_reflectors<T>(a, ep, vbuf_w, w, t + 1, li, nl);
       // this warp's stages of step t
       int32_t hi, lo;
       warp_stages(g, ep, w, t, &hi, &lo);
@@ -470,6 +519,9 @@ __device__ __forceinline__ bool process_unit(const ApplyArgs &a, int32_t e, int3
         const T *vb = vbuf_w + (int64_t)(t & 1) * ep.nb * a.ldv;
         if constexpr (BW > 0) {
           apply_stages_regwin<BW>(xw, mycol, a.ring, g, j, hi, lo, vb, sig, a.ldv);
+        } else if constexpr (BW < 0) {
+          for (int32_t s = hi; s >= lo; --s)
+            apply_pair(mycol, a.ring, g.row(s, j), g.len(s, j), vb + (int64_t)(sig - s) * a.ldv, lane & 1);
         } else {
           for (int32_t s = hi; s >= lo; --s)
             apply_one<T>(mycol, a.ring, g.row(s, j), g.len(s, j), vb + (int64_t)(sig - s) * a.ldv);
@@ -575,7 +627,10 @@ __global__ void __launch_bounds__(256, 1) batch_kernel(BatchArgs b) {
     const int *prevflag = un.prev >= 0 ? b.flags + un.prev : nullptr;
     const int32_t c0 = un.strip * 32;
     // (b = 64 real problems take the shared-memory window here: the 64-row
-    // register window would not fit beside the other paths of this kernel)
+    // register window would not fit beside the other paths of this kernel.
+    // Complex problems take one lane per column: two blocks of one warp per
+    // sweep already share an SM here, which is what lane pairs buy the
+    // single-problem kernel.)
     if (kind == kReal32)
       process_unit<double, 32>(a, un.epoch, c0, myflag, prevflag, true, smem_raw, &s_stop);
     else if (kind == kComplex)

@@ -24,6 +24,7 @@ struct BatchProblemHost {
   StoreGeom g;
   int64_t K = 0;
   int32_t ldv = 0, nb = 0, ring = 0, strips = 0, epochs = 0, kind = 0;
+  int32_t G = 0;  // sweeps per block
   size_t smem = 0;
   size_t store_off = 0, stage_off = 0;  // byte offsets in the shared buffers
 };
@@ -35,6 +36,7 @@ struct tbbt_batch {
   BatchGeom geom;
   int tuned = 0;
   size_t smem = 0;
+  int32_t threads = 0;  // one warp per sweep of a block
   int32_t grid = 0;
   int64_t nunits = 0;
   long long timeout_ns = 20000000000LL;
@@ -90,21 +92,24 @@ std::string batch_signature(const tbbt_batch *b) {
 tbbt_status batch_layout(tbbt_batch *b, const BatchGeom &geo) {
   b->geom = geo;
   size_t smem = 0, store = 0, stage = 0;
+  int32_t warps = 1;
   int64_t units = 0;
   for (auto &h : b->probs) {
     const bool cplx = h.p.dtype == TBBT_COMPLEX128;
     h.g = StoreGeom{(int32_t)h.p.n, (int32_t)h.p.nbw, cplx ? 1 : 0};
     h.K = h.g.num_reflectors();
     h.ldv = round_even((int32_t)h.p.nbw);
+    h.G = geo.G;
     h.nb = cplx ? geo.nb_cplx : geo.nb_real;
-    if (h.nb > 4 * geo.G) h.nb = 4 * geo.G;
-    h.ring = ring_rows_for((int32_t)h.p.nbw, geo.G, h.nb);
-    h.smem = smem_bytes_for(h.p.dtype, (int32_t)h.p.nbw, geo.G, h.nb);
+    if (h.nb > 4 * h.G) h.nb = 4 * h.G;
+    h.ring = ring_rows_for((int32_t)h.p.nbw, h.G, h.nb);
+    h.smem = smem_bytes_for(h.p.dtype, (int32_t)h.p.nbw, h.G, h.nb);
     if (h.smem > (size_t)kMaxSmem) return TBBT_ENOTSUP;
     smem = std::max(smem, h.smem);
+    warps = std::max(warps, h.G);
     h.kind = cplx ? tbbt::kComplex : (h.p.nbw == 32 ? tbbt::kReal32 : tbbt::kRealGeneric);
     h.strips = (int32_t)((h.p.nev + 31) / 32);
-    h.epochs = (h.g.num_sweeps() + geo.G - 1) / geo.G;
+    h.epochs = (h.g.num_sweeps() + h.G - 1) / h.G;
     if (h.p.nev == 0 || h.K == 0) h.strips = h.epochs = 0;
     h.store_off = store;
     store += round256((size_t)h.K * h.ldv * elem_size(h.p.dtype));
@@ -113,6 +118,7 @@ tbbt_status batch_layout(tbbt_batch *b, const BatchGeom &geo) {
     units += (int64_t)h.strips * h.epochs;
   }
   b->smem = smem;
+  b->threads = 32 * warps;
   b->nunits = units;
   return TBBT_OK;
 }
@@ -157,7 +163,7 @@ tbbt_status batch_build(tbbt_batch *b, const std::vector<void *> &qs, const std:
     a.g = h.g;
     a.nev = (int32_t)h.p.nev;
     a.ldv = h.ldv;
-    a.G = b->geom.G;
+    a.G = h.G;
     a.NB = h.nb;
     a.ring = h.ring;
     a.strips = h.strips;
@@ -197,7 +203,7 @@ tbbt_status batch_build(tbbt_batch *b, const std::vector<void *> &qs, const std:
   int dev = 0, sms = 0, per_sm = 0;
   TBBT_CUDA_TRY(cudaGetDevice(&dev));
   TBBT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  TBBT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tbbt::batch_kernel, b->geom.G * 32, b->smem));
+  TBBT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tbbt::batch_kernel, b->threads, b->smem));
   if (per_sm < 1) return TBBT_ENOTSUP;
   const int64_t resident = (int64_t)sms * per_sm;
   b->grid = (int32_t)std::max<int64_t>(1, std::min<int64_t>(b->nunits, resident));
@@ -228,7 +234,7 @@ tbbt_status batch_build(tbbt_batch *b, const std::vector<void *> &qs, const std:
     cudaMemsetAsync(b->d_flags, 0x7f, sizeof(int) * (size_t)b->nunits, cs);
     cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned), cs);
     tbbt::BatchArgs ba{b->d_probs, b->d_units, (int32_t)b->nunits, b->d_flags, b->d_counter, err};
-    tbbt::batch_kernel<<<(unsigned)b->grid, b->geom.G * 32, b->smem, cs>>>(ba);
+    tbbt::batch_kernel<<<(unsigned)b->grid, b->threads, b->smem, cs>>>(ba);
   }
   if (cudaStreamEndCapture(cs, &graph) != cudaSuccess || !graph) st = TBBT_ECUDA;
   if (st == TBBT_OK && cudaGraphInstantiate(&b->exec, graph, 0) != cudaSuccess) st = TBBT_ECUDA;

@@ -67,7 +67,7 @@ using ApplyFn = void (*)(tbbt::ApplyArgs);
 
 // The apply kernel instance for a data type and register-window width.
 ApplyFn apply_fn(tbbt_dtype dt, int32_t bw) {
-  if (dt == TBBT_COMPLEX128) return tbbt::apply_kernel<zdouble, 0>;
+  if (dt == TBBT_COMPLEX128) return tbbt::apply_kernel<zdouble, -1>;
   if (bw == 64) return tbbt::apply_kernel<double, 64>;
   if (bw == 32) return tbbt::apply_kernel<double, 32>;
   return tbbt::apply_kernel<double, 0>;
@@ -407,14 +407,15 @@ tbbt_status tbbt_plan_create(tbbt_plan **plan, tbbt_dtype dtype, int64_t n, int6
   p->K = p->g.num_reflectors();
   p->ldv = round_even((int32_t)nbw);
   // real data with b = 32 or 64 keep each column's window in registers
-  p->bw = (dtype == TBBT_REAL64 && (nbw == 32 || nbw == 64)) ? (int32_t)nbw : 0;
+  // complex data: two warps per sweep (a lane pair per column)
+  p->bw = (dtype == TBBT_REAL64 && (nbw == 32 || nbw == 64)) ? (int32_t)nbw : (dtype == TBBT_COMPLEX128 ? -1 : 0);
   // launch geometry: most sweeps per block that fit in shared memory
   // Default: 4 sweeps per block (one warp per SM sub-partition) and 8 stages
   // per step; two such blocks share an SM when they fit, so one block's
   // pipeline fill is covered by the other. Block widths that are not a
   // multiple of 4 load the sub-partitions unevenly and are slower.
   int32_t wantG = opt && opt->sweeps_per_block > 0 ? opt->sweeps_per_block : 4;
-  if (p->bw > 0 && wantG > 8) wantG = 8;  // 256 threads: room for the register window
+  if (p->bw != 0 && wantG > 8) wantG = 8;  // register window: 256 threads; lane pairs: 512
   int32_t wantNB = opt && opt->stages_per_step > 0 ? opt->stages_per_step : 8;
   if (wantG > 16) wantG = 16;
   int32_t G = wantG, NB = wantNB;
@@ -485,7 +486,8 @@ tbbt_status tbbt_plan_create(tbbt_plan **plan, tbbt_dtype dtype, int64_t n, int6
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return fail(TBBT_ECUDA);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_fn(dtype, p->bw), G * 32, p->smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_fn(dtype, p->bw), G * 32 * (p->bw < 0 ? 2 : 1),
+                                                      p->smem);
     if (e != cudaSuccess || per_sm < 1) return fail(TBBT_ECUDA);
     int64_t resident = (int64_t)sms * per_sm;
     p->grid = (int32_t)(p->units < resident ? p->units : resident);
@@ -571,7 +573,7 @@ tbbt_status tbbt_plan_execute(tbbt_plan *p, void *q, int64_t ldq, void *stream) 
   TBBT_CUDA_TRY(cudaMemsetAsync(p->d_flags, 0x7f, sizeof(int) * (size_t)p->units, s));
   TBBT_CUDA_TRY(cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned), s));
   unsigned blocks = (unsigned)p->grid;
-  apply_fn(p->dtype, p->bw)<<<blocks, p->G * 32, p->smem, s>>>(a);
+  apply_fn(p->dtype, p->bw)<<<blocks, p->G * 32 * (p->bw < 0 ? 2 : 1), p->smem, s>>>(a);
   TBBT_CUDA_TRY(cudaGetLastError());
   return TBBT_OK;
 }

@@ -77,7 +77,12 @@ def test_batch_matches_oracle_and_plans(P):
             q2 = col_major(X)
             plan.execute(q2)
             P.stream_check()
-            assert np.array_equal(q2.cpu().numpy(), got), (n, b, nev)
+            if np.iscomplexobj(X):
+                # the single-problem complex kernel sums v^H x in two halves
+                # (a lane pair per column), the batched one in one chain
+                assert np.abs(q2.cpu().numpy() - got).max() <= TOL, (n, b, nev)
+            else:
+                assert np.array_equal(q2.cpu().numpy(), got), (n, b, nev)
             plan.close()
     batch.close()
 
