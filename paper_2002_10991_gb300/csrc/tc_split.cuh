@@ -62,6 +62,7 @@ constexpr int FOP = 60;      // fixed-point exponent of V', U' and normalised W
 constexpr int STG_ROWS = 16;  // rows per staging box (16 x 8 bytes = one 128-byte swizzle row per column)
 constexpr int TMEM_COLS = 512;
 constexpr int REG_B = 224;   // second TMEM region (first one starts at column 0)
+constexpr int ZA_COL = 224;  // the Z digits (A operand of the first product), after its accumulators
 
 // offset of the balanced-digit form: 128 at every digit position + half a unit
 // of the last digit
@@ -85,10 +86,9 @@ struct Geo {
   static constexpr int UBYTES = P * UCHUNK;
   static constexpr int EBYTES = 128;                     // per-row exponents of U (int8)
   static constexpr int BLOCK_BYTES = VBYTES + UBYTES + EBYTES;
-  static constexpr int ZDIG = WS * RP * 2;               // one digit of the Z window [c][r]
+  static constexpr int ZCOLS = RP / 2;                   // TMEM columns of one Z digit (bf16 pairs)
   static constexpr int WDIG = WS * NB * 2;               // one digit of W [c][m]
-  static constexpr int OFF_Z = 0;                        // two Z digit buffers
-  static constexpr int OFF_W = OFF_Z + 2 * ZDIG;         // S W digit buffers
+  static constexpr int OFF_W = 0;                        // S W digit buffers
   static constexpr int OFF_V = OFF_W + S * WDIG;
   static constexpr int OFF_U = OFF_V + VBYTES;
   static constexpr int OFF_STG = (OFF_U + UBYTES + 1023) / 1024 * 1024;  // two swizzled boxes [c][16 rows]
@@ -150,6 +150,28 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                : "r"(taddr)
                : "memory");
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n" ::"r"(taddr), "r"(r[0]),
+               "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n" ::"r"(
+          taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
+// A operand in tensor memory: lane m = row m, K elements as bf16 pairs along the columns
+__device__ __forceinline__ void tc_mma_ta(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
 }
 template <int C>
 __device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&r)[C]) {
@@ -258,25 +280,31 @@ __device__ __forceinline__ uint2 digits4(const int64_t *x) {
   }
   return make_uint2(w[0], w[1]);
 }
+// digit K of R consecutive rows of one column -> R / 2 TMEM columns of the
+// thread's lane (bf16 pairs, the even row in the low half)
 template <int K, int R>
-__device__ __forceinline__ void store_digits(unsigned char *buf, int c, int row0, int kt, const int64_t (&z)[R]) {
-  // R consecutive K positions (row0 .. row0 + R - 1) of column c
+__device__ __forceinline__ void tmem_digits(uint32_t taddr, const int64_t (&z)[R]) {
+  uint32_t w[R / 2];
 #pragma unroll
   for (int q = 0; q < R / 8; ++q) {
     const uint4 v = digits8<K>(z + 8 * q);
-    *reinterpret_cast<uint4 *>(buf + kmaj(c, row0 + 8 * q, kt)) = v;
+    w[4 * q] = v.x;
+    w[4 * q + 1] = v.y;
+    w[4 * q + 2] = v.z;
+    w[4 * q + 3] = v.w;
   }
+  if constexpr (R == 16) tmem_st8(taddr, w);
+  else tmem_st16(taddr, w);
 }
 template <int R>
-__device__ __forceinline__ void store_z_digit(int k, unsigned char *buf, int c, int row0, int kt,
-                                              const int64_t (&z)[R]) {
+__device__ __forceinline__ void tmem_z_digit(int k, uint32_t taddr, const int64_t (&z)[R]) {
   switch (k) {
-    case 1: store_digits<1, R>(buf, c, row0, kt, z); break;
-    case 2: store_digits<2, R>(buf, c, row0, kt, z); break;
-    case 3: store_digits<3, R>(buf, c, row0, kt, z); break;
-    case 4: store_digits<4, R>(buf, c, row0, kt, z); break;
-    case 5: store_digits<5, R>(buf, c, row0, kt, z); break;
-    default: store_digits<6, R>(buf, c, row0, kt, z); break;
+    case 1: tmem_digits<1, R>(taddr, z); break;
+    case 2: tmem_digits<2, R>(taddr, z); break;
+    case 3: tmem_digits<3, R>(taddr, z); break;
+    case 4: tmem_digits<4, R>(taddr, z); break;
+    case 5: tmem_digits<5, R>(taddr, z); break;
+    default: tmem_digits<6, R>(taddr, z); break;
   }
 }
 
@@ -557,7 +585,7 @@ __device__ __forceinline__ void w_levels(uint32_t taddr, int64_t *w) {
 }
 
 struct TcBarriers {
-  uint64_t zfull[2], zfree[2], g1, wfull, c[3], cfree, v, u, stage, drain;
+  uint64_t zfull[S], blk, g1, wfull, c[3], cfree, v, u, stage, drain;
 };
 
 template <int B>
@@ -589,10 +617,8 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   if (tid == 0) {
-    mbar_init(&bars.zfull[0], D::NMATH);
-    mbar_init(&bars.zfull[1], D::NMATH);
-    mbar_init(&bars.zfree[0], 1);
-    mbar_init(&bars.zfree[1], 1);
+    for (int k = 0; k < S; ++k) mbar_init(&bars.zfull[k], D::NMATH);
+    mbar_init(&bars.blk, D::NMATH);
     mbar_init(&bars.g1, 1);
     mbar_init(&bars.wfull, D::NMATH);
     for (int p = 0; p < 3; ++p) mbar_init(&bars.c[p], 1);
@@ -610,7 +636,6 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
   const uint32_t tmem = s_tmem;
 
   // phase counters (each role counts the completions it waits for)
-  uint32_t n_z = 0;      // Z digit slices produced/consumed so far
   uint32_t n_blk = 0;    // blocks processed so far (g1, wfull, c[*], cfree)
   uint32_t n_v = 0, n_u = 0;  // producer: completions of the operand loads waited for
   uint32_t n_st = 0;          // staged row loads (issued by the producer, counted by every math thread)
@@ -651,7 +676,6 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
           mbar_expect_tx(&bars.u, D::UBYTES);
           bulk_load(smem + D::OFF_U, blkp + D::VBYTES, D::UBYTES, &bars.u);
           ++iss_u;
-          const uint32_t zbase = smem_u32(smem + D::OFF_Z);
           const uint32_t wbase = smem_u32(smem + D::OFF_W);
           const uint32_t vbase = smem_u32(smem + D::OFF_V);
           const uint32_t ubase = smem_u32(smem + D::OFF_U);
@@ -662,26 +686,24 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
             // GEMM1: level l = i + k (0-based), 32 TMEM columns per level
             bool ok = true;
             for (int k = 0; k < S; ++k) {
-              const uint32_t zb = n_z & 1;
-              if (!mbar_wait(&bars.zfull[zb], (n_z >> 1) & 1, &s_abort, a.err, a.timeout_ns)) {
+              if (!mbar_wait(&bars.zfull[k], n_blk & 1, &s_abort, a.err, a.timeout_ns)) {
                 ok = false;
                 break;
               }
-              ++n_z;
               tc_fence_after();
               const int ni = (S < LV - k) ? S : LV - k;  // V' slices paired with digit k
+              const uint32_t za = tmem + ZA_COL + D::ZCOLS * k;
               for (int ks = 0; ks < D::KS1; ++ks) {
-                const uint64_t ad = smem_desc(zbase + zb * D::ZDIG + ks * 256, D::SBO1);
                 const uint32_t bv = vbase + ks * 256;
                 if (k == 1 && ks == 0) {
                   // levels 1..5 accumulate; level 6 starts here (slice 5)
-                  tc_mma(tmem + 32, ad, smem_desc(bv, D::SBO1), idesc_bf16(5 * NB), 1);
-                  tc_mma(tmem + 32 * 6, ad, smem_desc(bv + 20 * D::SBO1, D::SBO1), idesc_bf16(NB), 0);
+                  tc_mma_ta(tmem + 32, za, smem_desc(bv, D::SBO1), idesc_bf16(5 * NB), 1);
+                  tc_mma_ta(tmem + 32 * 6, za, smem_desc(bv + 20 * D::SBO1, D::SBO1), idesc_bf16(NB), 0);
                 } else {
-                  tc_mma(tmem + 32 * k, ad, smem_desc(bv, D::SBO1), idesc_bf16(ni * NB), (k > 0 || ks > 0) ? 1u : 0u);
+                  tc_mma_ta(tmem + 32 * k, za + 8 * ks, smem_desc(bv, D::SBO1), idesc_bf16(ni * NB),
+                            (k > 0 || ks > 0) ? 1u : 0u);
                 }
               }
-              tc_commit(&bars.zfree[zb]);
             }
             if (!ok) break;
             tc_commit(&bars.g1);
@@ -814,20 +836,23 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
             }
             gv = __ldg(a.gvs + blk);
           }
-          // ---- digits of Z -> GEMM1
+          // ---- digits of Z -> GEMM1 (A operand in tensor memory). The columns
+          // are those of the previous block's second product: wait until every
+          // thread has read its correction.
           bool ok = true;
+          if (n_blk > 0) {
+            if (!mbar_wait(&bars.blk, (n_blk - 1) & 1, &s_abort, a.err, a.timeout_ns)) break;
+            tc_fence_after();
+          }
+          {
+            const uint32_t zt = tmem + lane_base + ZA_COL + prow / 2;
 #pragma unroll
-          for (int k = 1; k <= S; ++k) {  // unrolled: the digit helpers take k as a constant
-            const uint32_t zb = n_z & 1;
-            if (n_z >= 2 && !mbar_wait(&bars.zfree[zb], ((n_z >> 1) - 1) & 1, &s_abort, a.err, a.timeout_ns)) {
-              ok = false;
-              break;
+            for (int k = 1; k <= S; ++k) {  // unrolled: the digit helpers take k as a constant
+              tmem_z_digit<RT>(k, zt + D::ZCOLS * (k - 1), z);
+              tc_wait_st();
+              tc_fence_before();
+              mbar_arrive(&bars.zfull[k - 1]);
             }
-            store_z_digit<RT>(k, smem + D::OFF_Z + zb * D::ZDIG, col, prow, RP, z);
-            fence_proxy_async();
-            tc_fence_before();
-            mbar_arrive(&bars.zfull[zb]);
-            ++n_z;
           }
           if (!ok) break;
           // ---- W = V'^T Z for my column and my reflector range
@@ -935,10 +960,9 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
               z[r] -= shl_signed(t1[i], sh - 24) + shl_signed(t2[i], sh - 48);
             }
           }
-          if (P == 3 && p == P - 1) {  // region B is free for part 1
-            tc_fence_before();
-            mbar_arrive(&bars.cfree);
-          }
+          tc_fence_before();
+          if (P == 3 && p == P - 1) mbar_arrive(&bars.cfree);  // region B is free for part 1
+          mbar_arrive(&bars.blk);                                // my reads of this block's products are done
           ++n_blk;
           // ---- the part leaving the window: store it, take the new rows
           if (t + 1 < nblk && p == P - 1) {
