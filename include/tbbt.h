@@ -262,6 +262,38 @@ tbbt_status tbbt_stream_check(void *stream);
 tbbt_status tbbt_trans_ev_tridi_to_band_noalloc(tbbt_dtype dtype, const void *hh_v, const void *hh_tau, int64_t n,
                                                 int64_t nbw, int64_t nev, void *q, int64_t ldq, void *stream);
 
+/* -------------------------------------------------------------------------
+ * Band -> tridiagonal reduction by bulge chasing (Eq. 6b, Sec. 2.2.1,
+ * Fig. 2), the step whose reflectors the back-transformation applies: stage
+ * i = 0 .. n-3 has ceil((n-i-2)/nbw) sweeps, sweep j builds the Householder
+ * reflector of rows r = i+1+j*nbw .. r+L-1 (L = min(nbw, n-r); LAPACK
+ * convention H^H x = beta e_1, H = I - tau v v^H, v[0] = 1) that annihilates
+ * column i (j = 0) or the first column of the previous sweep's bulge, and
+ * applies it two-sided. Hermitian input gets one more stage, n-2, whose
+ * length-1 reflector makes the last sub-diagonal entry real, so d and e are
+ * real. The reflectors come out in the canonical store of the
+ * back-transformation calls, in generation order (stage-major), so the output
+ * can go straight to tbbt_trans_ev_tridi_to_band_d/_z or a plan.
+ *
+ * band:  device, lower band storage of the input, (nbw+1) x n column-major:
+ *        band[d + c*ldb] = B(c+d, c), d = 0 .. nbw (ldb >= nbw+1); entries
+ *        outside the matrix are ignored; the diagonal's imaginary part is
+ *        ignored. Not modified.
+ * hh_v, hh_tau: device outputs, K x nbw (column-major, reflector k at
+ *        hh_v[k*nbw ..], zeros beyond its length) and K, K = tbbt_num_reflectors.
+ * d, e:  device outputs, n and n-1 doubles (diagonal, sub-diagonal of T).
+ * The reduction runs in FP64 on the stream; a working copy of the band
+ * ((2 nbw + 1) x n elements) and small tables are allocated stream-ordered
+ * and released by the call. Errors: TBBT_EINVAL (shape, ldb, null pointer
+ * with n > 0), TBBT_ENOTSUP (nbw too wide for the shared-memory block:
+ * nbw > 118 complex), TBBT_ECUDA; bounded in-kernel waits record
+ * TBBT_ETIMEOUT (see tbbt_stream_check).
+ * ------------------------------------------------------------------------- */
+tbbt_status tbbt_bulge_chase_d(const double *band, int64_t ldb, int64_t n, int64_t nbw, double *hh_v, double *hh_tau,
+                               double *d, double *e, void *stream);
+tbbt_status tbbt_bulge_chase_z(const void *band, int64_t ldb, int64_t n, int64_t nbw, void *hh_v, void *hh_tau,
+                               double *d, double *e, void *stream);
+
 /* Host-side check of the block schedule (no GPU needed): largest number of
  * rows a thread block ever holds at once for these parameters, or -1 if the
  * schedule would touch a row twice in one step. Used by tests to show the

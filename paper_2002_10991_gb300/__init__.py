@@ -4,6 +4,7 @@ and this thin Python binding."""
 
 from .api import (  # noqa: F401
     Batch,
+    bulge_chase,
     Plan,
     TbbtError,
     num_reflectors,

@@ -92,6 +92,10 @@ def load():
                                       ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32)]
         L.tbbt_batch_destroy.restype = c_int
         L.tbbt_batch_destroy.argtypes = [p]
+        for name in ("tbbt_bulge_chase_d", "tbbt_bulge_chase_z"):
+            f = getattr(L, name)
+            f.restype = c_int
+            f.argtypes = [p, i64, i64, i64, p, p, p, p, p]
         L.tbbt_schedule_max_live_rows.restype = i64
         L.tbbt_schedule_max_live_rows.argtypes = [i64, i64, c_int, i32, i32]
         _lib = L

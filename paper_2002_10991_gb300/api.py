@@ -85,6 +85,39 @@ def trans_ev_tridi_to_band(hh_v, hh_tau, n: int, nbw: int, nev: int, q, ldq: int
     return q
 
 
+def bulge_chase(band, nbw: int | None = None, stream=None):
+    """Eq. 6b on the GPU: reduce the banded Hermitian matrix given in lower
+    band storage (CUDA tensor, shape (nbw+1, n), column-major: band[d, c] =
+    B[c+d, c]) to tridiagonal form. Returns (hh_v (K*nbw,), hh_tau (K,),
+    d (n,), e (n-1,)) as CUDA tensors; the store is in generation order, ready
+    for trans_ev_tridi_to_band or a Plan."""
+    import torch
+
+    cplx = _is_complex_dtype(band)
+    if nbw is None:
+        nbw = band.shape[0] - 1
+    n = band.shape[1]
+    if band.numel() and band.stride(0) != 1:
+        raise ValueError("band must be column-major (stride 1 along the band index)")
+    ldb = band.stride(1) if n > 1 else nbw + 1
+    K = num_reflectors(n, nbw, cplx)
+    dev = band.device
+    vdt = torch.complex128 if cplx else torch.float64
+    hh_v = torch.zeros(K * nbw, dtype=vdt, device=dev)
+    hh_tau = torch.zeros(K, dtype=vdt, device=dev)
+    d = torch.zeros(n, dtype=torch.float64, device=dev)
+    e = torch.zeros(max(n - 1, 0), dtype=torch.float64, device=dev)
+    L = _native.load()
+    f = L.tbbt_bulge_chase_z if cplx else L.tbbt_bulge_chase_d
+
+    def ptr(t):
+        return ctypes.c_void_p(t.data_ptr() if t.numel() else 0)
+
+    st = f(ptr(band), ldb, n, nbw, ptr(hh_v), ptr(hh_tau), ptr(d), ptr(e), _stream_handle(stream))
+    _check(st, "tbbt_bulge_chase")
+    return hh_v, hh_tau, d, e
+
+
 def trans_ev_tridi_to_band_host(hh_v, hh_tau, n: int, nbw: int, nev: int, q, ldq: int | None = None, stream=None,
                                 synchronize: bool = True):
     """The same with every array in host memory (numpy arrays or CPU

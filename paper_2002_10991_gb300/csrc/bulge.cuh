@@ -1,0 +1,315 @@
+// Band -> tridiagonal reduction by bulge chasing (Eq. 6b, Sec. 2.2.1): the
+// step that produces the reflector store the back-transformation consumes,
+// run on the GPU so that the store never leaves the device.
+//
+// Stage i (0-based) has ceil((n-i-2)/b) sweeps; sweep j works on rows
+// r = i+1+j*b .. r+L-1, L = min(b, n-r): it builds the Householder reflector
+// (LAPACK convention, H^H x = beta e_1, H = I - tau v v^H, v_0 = 1) of column
+// c (c = i for j = 0, c = r-b otherwise: the first column of the bulge left by
+// sweep j-1) and applies it two-sided (B <- H^H B H) to the entries of the
+// band it reaches:
+//   left:  rows r .. r+L-1, columns c+1 .. r-1          (A <- H^H A)
+//   block: rows and columns r .. r+L-1                   (D <- H^H D H)
+//   right: rows r+L .. min(r+L+b, n)-1, columns r .. r+L-1 (A <- A H)
+// Hermitian problems get one more stage, n-2, whose length-1 reflector makes
+// the last sub-diagonal entry real.
+//
+// Parallel schedule. Sweep j of stage i touches columns >= r_i(j) - b and
+// rows >= r_i(j); sweep j' of stage i+1 touches columns < r_{i+1}(j') + 2b
+// and rows < r_{i+1}(j') + 2b. So once stage i has finished sweeps 0 .. j'+2,
+// none of its remaining sweeps touch what sweep j' of stage i+1 reads or
+// writes, and all the sweeps that wrote it are done: stage i+1 runs sweep j'
+// when stage i has published progress >= min(j'+3, sweeps of stage i).
+// Persistent blocks claim stages in order from an atomic counter (a stage
+// only waits for a smaller one, claimed earlier by a running block), keep the
+// working band (lower storage, 2b+1 entries per column, L2-resident) in
+// global memory, and publish their progress after every sweep with a
+// release; the waits are bounded (TBBT_ETIMEOUT, then the block gives up).
+//
+// Within a sweep the three updates touch disjoint entries, so after the
+// reflector is built the block's warps share them: the left and right
+// updates one column / row per warp, the diagonal block in shared memory.
+#pragma once
+#include <stdint.h>
+
+#include "apply_kernels.cuh"
+
+namespace tbbt {
+namespace bc {
+
+template <typename T>
+struct Ops;
+template <>
+struct Ops<double> {
+  static __device__ __forceinline__ double conj(double x) { return x; }
+  static __device__ __forceinline__ double mul(double a, double b) { return a * b; }
+  static __device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
+  static __device__ __forceinline__ double re(double x) { return x; }
+  static __device__ __forceinline__ double im(double) { return 0.0; }
+  static __device__ __forceinline__ double make(double r, double) { return r; }
+  static __device__ __forceinline__ double zero() { return 0.0; }
+  static __device__ __forceinline__ double shfl_xor(double x, int o) { return __shfl_xor_sync(0xffffffffu, x, o); }
+};
+template <>
+struct Ops<zdouble> {
+  static __device__ __forceinline__ zdouble conj(zdouble x) { return zdouble{x.re, -x.im}; }
+  static __device__ __forceinline__ zdouble mul(zdouble a, zdouble b) {
+    return zdouble{fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)};
+  }
+  // a * b + c
+  static __device__ __forceinline__ zdouble fma_(zdouble a, zdouble b, zdouble c) {
+    zdouble r;
+    r.re = fma(a.re, b.re, c.re);
+    r.re = fma(-a.im, b.im, r.re);
+    r.im = fma(a.re, b.im, c.im);
+    r.im = fma(a.im, b.re, r.im);
+    return r;
+  }
+  static __device__ __forceinline__ double re(zdouble x) { return x.re; }
+  static __device__ __forceinline__ double im(zdouble x) { return x.im; }
+  static __device__ __forceinline__ zdouble make(double r, double i) { return zdouble{r, i}; }
+  static __device__ __forceinline__ zdouble zero() { return zdouble{0.0, 0.0}; }
+  static __device__ __forceinline__ zdouble shfl_xor(zdouble x, int o) {
+    return zdouble{__shfl_xor_sync(0xffffffffu, x.re, o), __shfl_xor_sync(0xffffffffu, x.im, o)};
+  }
+};
+template <typename T>
+__device__ __forceinline__ T add(T a, T b) {
+  return Ops<T>::make(Ops<T>::re(a) + Ops<T>::re(b), Ops<T>::im(a) + Ops<T>::im(b));
+}
+template <typename T>
+__device__ __forceinline__ T sub(T a, T b) {
+  return Ops<T>::make(Ops<T>::re(a) - Ops<T>::re(b), Ops<T>::im(a) - Ops<T>::im(b));
+}
+template <typename T>
+__device__ __forceinline__ T warp_sum(T x) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) x = add(x, Ops<T>::shfl_xor(x, o));
+  return x;
+}
+
+template <typename T>
+struct BcArgs {
+  T *w;             // working band, lower storage: (row, col) at w[(row - col) + col * ldw], ldw = 2b + 1
+  int64_t ldw;
+  StoreGeom g;
+  T *hh_v;          // canonical store, K x b
+  T *hh_tau;        // K
+  const int64_t *stage_off;  // first reflector of each stage
+  int32_t nstages;
+  int *progress;    // per stage: sweeps finished (published with release); kPoison if abandoned
+  unsigned *counter;
+  int *err;
+  long long timeout_ns;
+};
+
+constexpr int kBcMaxB = 128;
+
+template <typename T>
+__device__ __forceinline__ T *bat(const BcArgs<T> &a, int64_t row, int64_t col) {
+  return a.w + (row - col) + col * a.ldw;
+}
+// The working band is written by other SMs: read and write it at L2 (no
+// stale L1 lines from an earlier stage this block ran).
+__device__ __forceinline__ double ldw(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ zdouble ldw(const zdouble *p) {
+  const double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
+  return zdouble{v.x, v.y};
+}
+__device__ __forceinline__ void stw(double *p, double v) { __stcg(p, v); }
+__device__ __forceinline__ void stw(zdouble *p, zdouble v) { __stcg(reinterpret_cast<double2 *>(p), make_double2(v.re, v.im)); }
+
+// Hermitian entry (row, col) from the lower storage.
+template <typename T>
+__device__ __forceinline__ T hget(const BcArgs<T> &a, int64_t row, int64_t col) {
+  return row >= col ? ldw(bat(a, row, col)) : Ops<T>::conj(ldw(bat(a, col, row)));
+}
+
+// Bounded wait until a stage's published progress reaches need (1: give up).
+__device__ inline int wait_progress(int *err, long long timeout_ns, const int *flag, int need) {
+  const long long t0 = globaltimer_ns();
+  for (unsigned it = 0;; ++it) {
+    const int v = ld_acquire(flag);
+    if (v == kPoison) return 1;
+    if (v >= need) return 0;
+    if (*(volatile int *)err != 0) return 1;
+    if (globaltimer_ns() - t0 > timeout_ns) {
+      atomicCAS(err, 0, 4 /* TBBT_ETIMEOUT */);
+      return 1;
+    }
+    __nanosleep(it < 64 ? 32 : 256);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 1) bulge_kernel(BcArgs<T> a) {
+  using O = Ops<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = a.g.b;
+  T *sv = reinterpret_cast<T *>(smem_raw);  // reflector, b
+  T *sD = sv + kBcMaxB;                     // diagonal block, b x b (column-major, ld b)
+  T *sy = sD + (int64_t)b * b;              // work vector, b
+  __shared__ T s_tau;
+  __shared__ int s_stage;
+  __shared__ int s_stop;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int32_t n = a.g.n;
+  for (;;) {
+    if (tid == 0) {
+      s_stage = (int)atomicAdd(a.counter, 1u);
+      s_stop = (*(volatile int *)a.err != 0);
+    }
+    __syncthreads();
+    const int i = s_stage;
+    if (i >= a.nstages || s_stop) break;
+    const int32_t nsweep = (i <= n - 3) ? (n - i - 2 + b - 1) / b : 1;
+    const int32_t prev_sweeps = (i >= 1) ? ((i - 1 <= n - 3) ? (n - i - 1 + b - 1) / b : 1) : 0;
+    int *mine = a.progress + i;
+    bool abandoned = false;
+    for (int32_t j = 0; j < nsweep; ++j) {
+      // the previous stage must be 3 sweeps ahead (or finished)
+      if (tid == 0 && i >= 1) {
+        const int need = min(j + 3, prev_sweeps);
+        s_stop = wait_progress(a.err, a.timeout_ns, a.progress + i - 1, need);
+      }
+      __syncthreads();
+      if (s_stop) {
+        abandoned = true;
+        break;
+      }
+      const int64_t r = i + 1 + (int64_t)j * b;
+      const int L = (int)((n - r < b) ? n - r : b);
+      const int64_t c = (j == 0) ? i : r - b;
+      // ---- the reflector of column c, rows r .. r+L-1 (one warp)
+      if (warp == 0) {
+        double s2 = 0.0;
+        for (int t = 1 + lane; t < L; t += 32) {
+          const T x = ldw(bat(a, r + t, c));
+          s2 = fma(O::re(x), O::re(x), s2);
+          s2 = fma(O::im(x), O::im(x), s2);
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        const T alpha = ldw(bat(a, r, c));
+        T tau, scal;
+        double beta;
+        if (s2 == 0.0 && O::im(alpha) == 0.0) {
+          tau = O::zero();
+          beta = O::re(alpha);
+          scal = O::zero();
+        } else {
+          const double nrm = sqrt(O::re(alpha) * O::re(alpha) + O::im(alpha) * O::im(alpha) + s2);
+          beta = O::re(alpha) >= 0.0 ? -nrm : nrm;
+          // tau = (beta - alpha) / beta, scal = 1 / (alpha - beta)
+          tau = O::make((beta - O::re(alpha)) / beta, -O::im(alpha) / beta);
+          const double dr = O::re(alpha) - beta, di = O::im(alpha);
+          const double den = dr * dr + di * di;
+          scal = O::make(dr / den, -di / den);
+        }
+        for (int t = lane; t < L; t += 32) {
+          T vt;
+          if (t == 0) vt = O::make(1.0, 0.0);
+          else vt = (O::re(scal) == 0.0 && O::im(scal) == 0.0) ? O::zero() : O::mul(ldw(bat(a, r + t, c)), scal);
+          sv[t] = vt;
+        }
+        __syncwarp();
+        for (int t = lane; t < L; t += 32) stw(bat(a, r + t, c), (t == 0) ? O::make(beta, 0.0) : O::zero());
+        if (lane == 0) s_tau = tau;
+        // the canonical store
+        const int64_t k = a.stage_off[i] + j;
+        for (int t = lane; t < b; t += 32) a.hh_v[k * b + t] = (t < L) ? sv[t] : O::zero();
+        if (lane == 0) a.hh_tau[k] = tau;
+      }
+      __syncthreads();
+      const T tau = s_tau;
+      const T ctau = O::conj(tau);
+      // ---- left: rows r .. r+L-1, columns c+1 .. r-1 (a warp per column)
+      for (int64_t col = c + 1 + warp; col < r; col += nw) {
+        T wsum = O::zero();
+        for (int t = lane; t < L; t += 32) wsum = O::fma_(O::conj(sv[t]), ldw(bat(a, r + t, col)), wsum);
+        wsum = warp_sum(wsum);
+        const T f = O::mul(ctau, wsum);
+        for (int t = lane; t < L; t += 32) {
+          T *p = bat(a, r + t, col);
+          stw(p, sub(ldw(p), O::mul(f, sv[t])));
+        }
+      }
+      // ---- right: rows r+L .. min(r+L+b, n)-1, columns r .. r+L-1 (a warp per row)
+      const int64_t rend = (r + L + b < n) ? r + L + b : n;
+      for (int64_t row = r + L + warp; row < rend; row += nw) {
+        T wsum = O::zero();
+        for (int t = lane; t < L; t += 32) wsum = O::fma_(ldw(bat(a, row, r + t)), sv[t], wsum);
+        wsum = warp_sum(wsum);
+        const T f = O::mul(tau, wsum);
+        for (int t = lane; t < L; t += 32) {
+          T *p = bat(a, row, r + t);
+          stw(p, sub(ldw(p), O::mul(f, O::conj(sv[t]))));
+        }
+      }
+      // ---- the diagonal block: D <- D H, then D <- H^H D (in shared memory)
+      for (int idx = tid; idx < L * L; idx += blockDim.x) {
+        const int t = idx % L, s = idx / L;
+        sD[t + s * b] = hget(a, r + t, r + s);
+      }
+      __syncthreads();
+      for (int t = tid; t < L; t += blockDim.x) {  // y = D v
+        T acc = O::zero();
+        for (int s = 0; s < L; ++s) acc = O::fma_(sD[t + s * b], sv[s], acc);
+        sy[t] = acc;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < L * L; idx += blockDim.x) {  // D -= tau y v^H
+        const int t = idx % L, s = idx / L;
+        sD[t + s * b] = sub(sD[t + s * b], O::mul(O::mul(tau, sy[t]), O::conj(sv[s])));
+      }
+      __syncthreads();
+      for (int s = tid; s < L; s += blockDim.x) {  // y = v^H D
+        T acc = O::zero();
+        for (int t = 0; t < L; ++t) acc = O::fma_(O::conj(sv[t]), sD[t + s * b], acc);
+        sy[s] = acc;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < L * L; idx += blockDim.x) {  // D -= conj(tau) v y, lower part back
+        const int t = idx % L, s = idx / L;
+        if (t >= s) {
+          T dv = sub(sD[t + s * b], O::mul(O::mul(ctau, sv[t]), sy[s]));
+          if (t == s) dv = O::make(O::re(dv), 0.0);
+          stw(bat(a, r + t, r + s), dv);
+        }
+      }
+      __syncthreads();
+      // sweep j of stage i is done: its entries are final for the next stage
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) st_release(mine, j + 1);
+    }
+    if (abandoned && tid == 0) st_release(mine, kPoison);
+    __syncthreads();
+  }
+}
+
+// Diagonal and (real) sub-diagonal of the reduced band.
+template <typename T>
+__global__ void bulge_extract_kernel(const T *w, int64_t ldw, int32_t n, double *d, double *e) {
+  const int64_t cidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cidx >= n) return;
+  d[cidx] = Ops<T>::re(w[cidx * ldw]);
+  if (cidx + 1 < n) e[cidx] = Ops<T>::re(w[1 + cidx * ldw]);
+}
+
+// Working band from the caller's lower band storage (b+1) x n (ldb >= b+1);
+// zero fill beyond, real diagonal.
+template <typename T>
+__global__ void bulge_load_kernel(const T *band, int64_t ldb, T *w, int64_t ldw, int32_t n, int32_t b) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t total = (int64_t)n * ldw;
+  if (idx >= total) return;
+  const int64_t col = idx / ldw, dd = idx - col * ldw;
+  T val = Ops<T>::zero();
+  if (dd <= b && col + dd < n) val = band[dd + col * ldb];
+  if (dd == 0) val = Ops<T>::make(Ops<T>::re(val), 0.0);
+  w[idx] = val;
+}
+
+}  // namespace bc
+}  // namespace tbbt

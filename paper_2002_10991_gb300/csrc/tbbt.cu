@@ -18,6 +18,7 @@
 #include "apply_kernels.cuh"
 #include "split_kernels.cuh"
 #include "tc_split.cuh"
+#include "bulge.cuh"
 
 using tbbt::StoreGeom;
 using tbbt::zdouble;
@@ -890,3 +891,111 @@ extern "C" tbbt_status tbbt_trans_ev_tridi_to_band_noalloc(tbbt_dtype dtype, con
   if (dtype == TBBT_COMPLEX128) return noalloc_launch<zdouble>(*d, dtype, hh_v, hh_tau, n, nbw, nev, q, ldq, s);
   return noalloc_launch<double>(*d, dtype, hh_v, hh_tau, n, nbw, nev, q, ldq, s);
 }
+
+// ---------------------------------------------------------------------------
+// band -> tridiagonal reduction (bulge chasing) on the GPU
+// ---------------------------------------------------------------------------
+namespace {
+template <typename T>
+tbbt_status bulge_chase_impl(const T *band, int64_t ldb, int64_t n, int64_t nbw, T *hh_v, T *hh_tau, double *d,
+                             double *e, cudaStream_t s) {
+  const bool cplx = sizeof(T) == 16;
+  tbbt_status st = check_shape(n, nbw, 0);
+  if (st != TBBT_OK) return st;
+  if (ldb < nbw + 1) return TBBT_EINVAL;
+  if (n == 0) return TBBT_OK;
+  if (!band || !d) return TBBT_EINVAL;
+  if (n > 1 && !e) return TBBT_EINVAL;
+  const StoreGeom g{(int32_t)n, (int32_t)nbw, cplx ? 1 : 0};
+  const int64_t K = g.num_reflectors();
+  if (K > 0 && (!hh_v || !hh_tau)) return TBBT_EINVAL;
+  const size_t smem = (size_t)(tbbt::bc::kBcMaxB + nbw * nbw + nbw) * sizeof(T);
+  if (smem > (size_t)kMaxSmem) return TBBT_ENOTSUP;
+  const int64_t ldw = 2 * nbw + 1;
+  const int32_t nstages = cplx ? (n >= 2 ? (int32_t)n - 1 : 0) : (n >= 3 ? (int32_t)n - 2 : 0);
+  std::vector<int64_t> off((size_t)std::max<int32_t>(nstages, 1), 0);
+  {
+    int64_t k = 0;
+    for (int32_t i = 0; i < nstages; ++i) {
+      off[(size_t)i] = k;
+      k += (i <= n - 3) ? (n - i - 2 + nbw - 1) / nbw : 1;
+    }
+  }
+  T *w = nullptr;
+  int64_t *d_off = nullptr;
+  int *progress = nullptr;  // nstages flags + the claim counter
+  TBBT_CUDA_TRY(cudaMallocAsync((void **)&w, sizeof(T) * (size_t)ldw * (size_t)n, s));
+  cudaError_t ce = cudaMallocAsync((void **)&d_off, sizeof(int64_t) * off.size(), s);
+  if (ce == cudaSuccess) ce = cudaMallocAsync((void **)&progress, sizeof(int) * ((size_t)nstages + 1), s);
+  if (ce != cudaSuccess) {
+    (void)cudaGetLastError();
+    if (w) cudaFreeAsync(w, s);
+    if (d_off) cudaFreeAsync(d_off, s);
+    return TBBT_ENOMEM;
+  }
+  tbbt_status rs = TBBT_OK;
+  do {
+    if (cudaMemcpyAsync(d_off, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(progress, 0, sizeof(int) * ((size_t)nstages + 1), s) != cudaSuccess) {
+      rs = TBBT_ECUDA;
+      break;
+    }
+    const int64_t total = ldw * n;
+    tbbt::bc::bulge_load_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(band, ldb, w, ldw, (int32_t)n,
+                                                                                 (int32_t)nbw);
+    if (cudaGetLastError() != cudaSuccess) {
+      rs = TBBT_ECUDA;
+      break;
+    }
+    if (nstages > 0) {
+      if (cudaFuncSetAttribute(tbbt::bc::bulge_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess) {
+        rs = TBBT_ECUDA;
+        break;
+      }
+      int dev = 0, sms = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      tbbt::bc::BcArgs<T> a;
+      a.w = w;
+      a.ldw = ldw;
+      a.g = g;
+      a.hh_v = hh_v;
+      a.hh_tau = hh_tau;
+      a.stage_off = d_off;
+      a.nstages = nstages;
+      a.progress = progress;
+      a.counter = reinterpret_cast<unsigned *>(progress + nstages);
+      int *err = nullptr;
+      cudaGetSymbolAddress((void **)&err, g_tbbt_error);
+      a.err = err;
+      a.timeout_ns = 20000000000LL;
+      const int grid = std::min<int32_t>(nstages, sms > 0 ? sms : 1);
+      tbbt::bc::bulge_kernel<T><<<grid, 256, smem, s>>>(a);
+      if (cudaGetLastError() != cudaSuccess) {
+        rs = TBBT_ECUDA;
+        break;
+      }
+    }
+    tbbt::bc::bulge_extract_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w, ldw, (int32_t)n, d, e);
+    if (cudaGetLastError() != cudaSuccess) rs = TBBT_ECUDA;
+  } while (0);
+  cudaFreeAsync(w, s);
+  cudaFreeAsync(d_off, s);
+  cudaFreeAsync(progress, s);
+  return rs;
+}
+}  // namespace
+
+extern "C" {
+tbbt_status tbbt_bulge_chase_d(const double *band, int64_t ldb, int64_t n, int64_t nbw, double *hh_v, double *hh_tau,
+                               double *d, double *e, void *stream) {
+  return bulge_chase_impl<double>(band, ldb, n, nbw, hh_v, hh_tau, d, e, (cudaStream_t)stream);
+}
+tbbt_status tbbt_bulge_chase_z(const void *band, int64_t ldb, int64_t n, int64_t nbw, void *hh_v, void *hh_tau,
+                               double *d, double *e, void *stream) {
+  return bulge_chase_impl<zdouble>((const zdouble *)band, ldb, n, nbw, (zdouble *)hh_v, (zdouble *)hh_tau, d, e,
+                                   (cudaStream_t)stream);
+}
+}  // extern "C"
+
