@@ -223,27 +223,52 @@ __global__ void __launch_bounds__(256, 1) bulge_kernel(BcArgs<T> a) {
       __syncthreads();
       const T tau = s_tau;
       const T ctau = O::conj(tau);
-      // ---- left: rows r .. r+L-1, columns c+1 .. r-1 (a warp per column)
-      for (int64_t col = c + 1 + warp; col < r; col += nw) {
-        T wsum = O::zero();
-        for (int t = lane; t < L; t += 32) wsum = O::fma_(O::conj(sv[t]), ldw(bat(a, r + t, col)), wsum);
-        wsum = warp_sum(wsum);
-        const T f = O::mul(ctau, wsum);
-        for (int t = lane; t < L; t += 32) {
-          T *p = bat(a, r + t, col);
-          stw(p, sub(ldw(p), O::mul(f, sv[t])));
-        }
-      }
-      // ---- right: rows r+L .. min(r+L+b, n)-1, columns r .. r+L-1 (a warp per row)
-      const int64_t rend = (r + L + b < n) ? r + L + b : n;
-      for (int64_t row = r + L + warp; row < rend; row += nw) {
-        T wsum = O::zero();
-        for (int t = lane; t < L; t += 32) wsum = O::fma_(ldw(bat(a, row, r + t)), sv[t], wsum);
-        wsum = warp_sum(wsum);
-        const T f = O::mul(tau, wsum);
-        for (int t = lane; t < L; t += 32) {
-          T *p = bat(a, row, r + t);
-          stw(p, sub(ldw(p), O::mul(f, O::conj(sv[t]))));
+      // ---- left: rows r .. r+L-1, columns c+1 .. r-1, and right: rows
+      // r+L .. min(r+L+b, n)-1, columns r .. r+L-1. A warp takes CB columns
+      // (rows) at a time: all their loads are issued before the reductions,
+      // and the values stay in registers for the update (one L2 round trip
+      // per batch instead of two per column).
+      {
+        constexpr int CB = 4;          // columns (rows) per batch
+        constexpr int EPL = kBcMaxB / 32;  // elements per lane, at most
+        const int64_t ncl = r - (c + 1);  // left columns
+        const int64_t rend = (r + L + b < n) ? r + L + b : n;
+        const int64_t nrr = rend - (r + L);  // right rows
+        const int64_t nbl = (ncl + CB - 1) / CB, nbr = (nrr + CB - 1) / CB;
+        for (int64_t bi = warp; bi < nbl + nbr; bi += nw) {
+          const bool left = bi < nbl;
+          const int64_t first = left ? c + 1 + bi * CB : r + L + (bi - nbl) * CB;
+          const int64_t last = left ? r : rend;  // exclusive
+          T x[CB][EPL];
+#pragma unroll
+          for (int q = 0; q < CB; ++q)
+#pragma unroll
+            for (int e = 0; e < EPL; ++e) {
+              const int t = lane + 32 * e;
+              const int64_t k = first + q;
+              x[q][e] = (k < last && t < L) ? ldw(left ? bat(a, r + t, k) : bat(a, k, r + t)) : O::zero();
+            }
+#pragma unroll
+          for (int q = 0; q < CB; ++q) {
+            const int64_t k = first + q;
+            T wsum = O::zero();
+#pragma unroll
+            for (int e = 0; e < EPL; ++e) {
+              const int t = lane + 32 * e;
+              if (t < L) wsum = left ? O::fma_(O::conj(sv[t]), x[q][e], wsum) : O::fma_(x[q][e], sv[t], wsum);
+            }
+            wsum = warp_sum(wsum);
+            if (k >= last) continue;
+            const T f = O::mul(left ? ctau : tau, wsum);
+#pragma unroll
+            for (int e = 0; e < EPL; ++e) {
+              const int t = lane + 32 * e;
+              if (t < L) {
+                if (left) stw(bat(a, r + t, k), sub(x[q][e], O::mul(f, sv[t])));
+                else stw(bat(a, k, r + t), sub(x[q][e], O::mul(f, O::conj(sv[t]))));
+              }
+            }
+          }
         }
       }
       // ---- the diagonal block: D <- D H, then D <- H^H D (in shared memory)
