@@ -125,6 +125,9 @@ __device__ __forceinline__ T hget(const BcArgs<T> &a, int64_t row, int64_t col) 
   return row >= col ? ldw(bat(a, row, col)) : Ops<T>::conj(ldw(bat(a, col, row)));
 }
 
+// Barrier among the first `count` threads of the block (id 1; id 0 is __syncthreads).
+__device__ __forceinline__ void bar_sub(int count) { asm volatile("bar.sync 1, %0;\n" ::"r"(count) : "memory"); }
+
 // Bounded wait until a stage's published progress reaches need (1: give up).
 __device__ inline int wait_progress(int *err, long long timeout_ns, const int *flag, int need) {
   const long long t0 = globaltimer_ns();
@@ -223,19 +226,20 @@ __global__ void __launch_bounds__(256, 1) bulge_kernel(BcArgs<T> a) {
       __syncthreads();
       const T tau = s_tau;
       const T ctau = O::conj(tau);
-      // ---- left: rows r .. r+L-1, columns c+1 .. r-1, and right: rows
-      // r+L .. min(r+L+b, n)-1, columns r .. r+L-1. A warp takes CB columns
-      // (rows) at a time: all their loads are issued before the reductions,
-      // and the values stay in registers for the update (one L2 round trip
-      // per batch instead of two per column).
-      {
-        constexpr int CB = 4;          // columns (rows) per batch
+      // The left / right updates (warps 4..7) and the diagonal block (warps
+      // 0..3) touch disjoint entries and run side by side.
+      if (warp >= 4) {
+        // ---- left: rows r .. r+L-1, columns c+1 .. r-1, and right: rows
+        // r+L .. min(r+L+b, n)-1, columns r .. r+L-1. A warp takes CB columns
+        // (rows) at a time: all their loads are issued before the reductions,
+        // and the values stay in registers for the update.
+        constexpr int CB = 4;              // columns (rows) per batch
         constexpr int EPL = kBcMaxB / 32;  // elements per lane, at most
-        const int64_t ncl = r - (c + 1);  // left columns
+        const int64_t ncl = r - (c + 1);   // left columns
         const int64_t rend = (r + L + b < n) ? r + L + b : n;
         const int64_t nrr = rend - (r + L);  // right rows
         const int64_t nbl = (ncl + CB - 1) / CB, nbr = (nrr + CB - 1) / CB;
-        for (int64_t bi = warp; bi < nbl + nbr; bi += nw) {
+        for (int64_t bi = warp - 4; bi < nbl + nbr; bi += nw - 4) {
           const bool left = bi < nbl;
           const int64_t first = left ? c + 1 + bi * CB : r + L + (bi - nbl) * CB;
           const int64_t last = left ? r : rend;  // exclusive
@@ -270,42 +274,42 @@ __global__ void __launch_bounds__(256, 1) bulge_kernel(BcArgs<T> a) {
             }
           }
         }
-      }
-      // ---- the diagonal block: D <- D H, then D <- H^H D (in shared memory)
-      for (int idx = tid; idx < L * L; idx += blockDim.x) {
-        const int t = idx % L, s = idx / L;
-        sD[t + s * b] = hget(a, r + t, r + s);
-      }
-      __syncthreads();
-      for (int t = tid; t < L; t += blockDim.x) {  // y = D v
-        T acc = O::zero();
-        for (int s = 0; s < L; ++s) acc = O::fma_(sD[t + s * b], sv[s], acc);
-        sy[t] = acc;
-      }
-      __syncthreads();
-      for (int idx = tid; idx < L * L; idx += blockDim.x) {  // D -= tau y v^H
-        const int t = idx % L, s = idx / L;
-        sD[t + s * b] = sub(sD[t + s * b], O::mul(O::mul(tau, sy[t]), O::conj(sv[s])));
-      }
-      __syncthreads();
-      for (int s = tid; s < L; s += blockDim.x) {  // y = v^H D
-        T acc = O::zero();
-        for (int t = 0; t < L; ++t) acc = O::fma_(O::conj(sv[t]), sD[t + s * b], acc);
-        sy[s] = acc;
-      }
-      __syncthreads();
-      for (int idx = tid; idx < L * L; idx += blockDim.x) {  // D -= conj(tau) v y, lower part back
-        const int t = idx % L, s = idx / L;
-        if (t >= s) {
-          T dv = sub(sD[t + s * b], O::mul(O::mul(ctau, sv[t]), sy[s]));
-          if (t == s) dv = O::make(O::re(dv), 0.0);
-          stw(bat(a, r + t, r + s), dv);
+      } else {
+        // ---- the diagonal block, D <- H^H D H = D - tau y v^H - conj(tau) v y^H
+        // + |tau|^2 (v^H y) v v^H with y = D v (D Hermitian: v^H D = y^H)
+        const int bt = tid;  // 0 .. 127
+        for (int idx = bt; idx < L * L; idx += 128) {
+          const int t = idx % L, s2 = idx / L;
+          sD[t + s2 * b] = hget(a, r + t, r + s2);
+        }
+        bar_sub(128);
+        for (int t = bt; t < L; t += 128) {
+          T acc = O::zero();
+          for (int s2 = 0; s2 < L; ++s2) acc = O::fma_(sD[t + s2 * b], sv[s2], acc);
+          sy[t] = acc;
+        }
+        bar_sub(128);
+        double al = 0.0;  // v^H y (real)
+        for (int t = 0; t < L; ++t) {
+          const T p2 = O::mul(O::conj(sv[t]), sy[t]);
+          al += O::re(p2);
+        }
+        const double tt2 = O::re(tau) * O::re(tau) + O::im(tau) * O::im(tau);
+        const double cfac = tt2 * al;
+        for (int idx = bt; idx < L * L; idx += 128) {
+          const int t = idx % L, s2 = idx / L;
+          if (t < s2) continue;
+          T dv = sD[t + s2 * b];
+          dv = sub(dv, O::mul(O::mul(tau, sy[t]), O::conj(sv[s2])));
+          dv = sub(dv, O::mul(O::mul(ctau, sv[t]), O::conj(sy[s2])));
+          dv = add(dv, O::mul(O::make(cfac, 0.0), O::mul(sv[t], O::conj(sv[s2]))));
+          if (t == s2) dv = O::make(O::re(dv), 0.0);
+          stw(bat(a, r + t, r + s2), dv);
         }
       }
       __syncthreads();
       // sweep j of stage i is done: its entries are final for the next stage
-      __threadfence();
-      __syncthreads();
+      // (the barrier above orders every thread's stores before this release)
       if (tid == 0) st_release(mine, j + 1);
     }
     if (abandoned && tid == 0) st_release(mine, kPoison);
