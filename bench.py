@@ -97,13 +97,70 @@ SPLIT_KERNEL = {"split": "tbbt::split::split_apply_kernel<{b}>", "split-tc": "tb
 
 
 BATCH_WORKLOAD = "batch-64-mixed"
+# band -> tridiagonal on the GPU (the step that produces the store), DFT-like band
+BULGE_WORKLOADS = {"bulge-real-n4096-b64": (4096, 64, False), "bulge-complex-n4096-b64": (4096, 64, True),
+                   "bulge-real-n8192-b64": (8192, 64, False)}
 
 
 def set_workload(name: str):
     global WORKLOAD
-    if name not in I.WORKLOADS and name != BATCH_WORKLOAD:
+    if name not in I.WORKLOADS and name != BATCH_WORKLOAD and name not in BULGE_WORKLOADS:
         raise SystemExit(f"unknown workload {name}")
     WORKLOAD = name
+
+
+def bulge_bench(args):
+    """Band -> tridiagonal reduction by bulge chasing (Eq. 6b) on the GPU
+    against the oracle's reduction on the host (single-threaded C), on a
+    seeded DFT-like band; parity of d, e, tau and v against the oracle."""
+    import torch
+
+    import paper_2002_10991_gb300 as P
+
+    import oracle
+
+    torch.cuda.set_device(0)
+    n, b, cplx = BULGE_WORKLOADS[WORKLOAD]
+    W = I.band_dft(n, b, 2002109910 + n, cplx)
+    band = torch.from_numpy(np.ascontiguousarray(W.T)).cuda().t()
+    for _ in range(max(args.warmup, 1)):
+        P.bulge_chase(band)
+    P.stream_check()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clocks:
+        e0.record(stream)
+        for _ in range(args.steps):
+            out = P.bulge_chase(band)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    P.stream_check()
+    ms = e0.elapsed_time(e1) / args.steps
+    v, tau, d, e = (x.cpu().numpy() for x in out)
+    t0 = time.perf_counter()
+    vo, to, do, eo = oracle.bulge_chase(W)
+    cpu_s = time.perf_counter() - t0
+    K = len(tau)
+    # real flops of the reduction, counted from the store: a reflector of length L is applied from the
+    # right to the L x b block below its diagonal block and from the left to the b columns beside it
+    # (4 L b each) and two-sidedly to its L x L diagonal block (4 L^2); a complex flop counts 4
+    L = I.store_lengths(n, b, cplx).astype(np.float64)
+    flops = float(np.sum((4.0 if cplx else 1.0) * (8 * L * b + 4 * L * L)))
+    line = {
+        "metric": "band->tridiagonal (bulge chasing) time", "value": ms, "unit": "ms", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128" if cplx else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "nbw": b, "reflectors": K, "band": "seeded DFT-like band"},
+        "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "tbbt::bc::bulge_kernel", "note": "latency-bound: a chain of dependent sweeps"},
+        "cpu_baseline": {"value": cpu_s * 1e3, "unit": "ms", "cores": 1, "kind": "oracle",
+                         "sample": "the whole reduction, single-threaded C"},
+        "parity": {"max_abs_d": float(np.abs(d - do).max()), "max_abs_e": float(np.abs(e - eo).max(initial=0)),
+                   "max_abs_tau": float(np.abs(tau - to).max(initial=0)), "max_abs_v": float(np.abs(v - vo).max(initial=0))},
+        "speedup_vs_cpu_oracle": cpu_s * 1e3 / ms, "gpu_launches": 3 * args.steps, "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
 
 
 def batch_bench(args):
@@ -358,8 +415,8 @@ def main():
                     help="fp64 runs of real b=32/64 workloads: also time this many steps of the tcgen05 "
                          "split-precision form on the same inputs (0: skip)")
     ap.add_argument("--workload", default=WORKLOAD,
-                    help="named workload (default: the benchmark workload; others are for profiler captures "
-                         "and the batched-form measurement)")
+                    help="named workload (default: the benchmark workload; others are for profiler captures, "
+                         "the batched-form measurement and the GPU bulge chase: " + ", ".join(BULGE_WORKLOADS) + ")")
     ap.add_argument("--autotune", action="store_true", help="batched workload: tune the launch geometry first")
     ap.add_argument("--variant", default="fp64", choices=list(VARIANTS),
                     help="fp64: reflector-by-reflector FP64 kernel; split: WY blocks on BF16 tensor cores "
@@ -370,6 +427,9 @@ def main():
     set_workload(args.workload)
     if WORKLOAD == BATCH_WORKLOAD:
         batch_bench(args)
+        return
+    if WORKLOAD in BULGE_WORKLOADS:
+        bulge_bench(args)
         return
     world, rank, local = dist_setup()
 
@@ -568,6 +628,7 @@ def main():
                 "ms_per_step": sms, "steps": split_tc["steps"], "speedup_vs_fp64": ms_per_step / sms,
                 "fp64_equivalent_tflops": flops / (sms * 1e-3) / 1e12,
                 "tensor_tflops": tc_tensor_flops(w) / (sms * 1e-3) / 1e12,
+                "tensor_frac_of_bf16_peak": tc_tensor_flops(w) / (sms * 1e-3) / 1e12 / BF16_PEAK_TFLOPS,
                 "max_abs_err_vs_oracle": float(np.abs(Zo - split_tc["cols"]).max()),
                 "err_sample": cpu["sample"],
             }
