@@ -109,10 +109,26 @@ def set_workload(name: str):
     WORKLOAD = name
 
 
+def bulge_parity(d, e, do, eo):
+    """What is unique in a tridiagonal reduction of this band. The signs of e,
+    and with them tau and v, follow the rounding of near-zero bulge entries,
+    and d itself moves by ~1e-7 under a 1e-15 relative perturbation of the
+    n=8192 band; the spectrum of T and |e| are what two correct reductions
+    share."""
+    from scipy.linalg import eigvalsh_tridiagonal
+
+    lam = eigvalsh_tridiagonal(d, e) if len(d) > 1 else d
+    lam_o = eigvalsh_tridiagonal(do, eo) if len(do) > 1 else do
+    return {"max_abs_eig_T": float(np.abs(lam - lam_o).max(initial=0)),
+            "max_abs_eig_T_rel": float(np.abs(lam - lam_o).max(initial=0) / max(np.abs(lam_o).max(initial=0), 1e-300)),
+            "max_abs_d": float(np.abs(d - do).max(initial=0)),
+            "max_abs_abs_e": float(np.abs(np.abs(e) - np.abs(eo)).max(initial=0))}
+
+
 def bulge_bench(args):
     """Band -> tridiagonal reduction by bulge chasing (Eq. 6b) on the GPU
     against the oracle's reduction on the host (single-threaded C), on a
-    seeded DFT-like band; parity of d, e, tau and v against the oracle."""
+    seeded DFT-like band; parity of the tridiagonal matrix against the oracle's."""
     import torch
 
     import paper_2002_10991_gb300 as P
@@ -136,11 +152,11 @@ def bulge_bench(args):
         torch.cuda.synchronize()
     P.stream_check()
     ms = e0.elapsed_time(e1) / args.steps
-    v, tau, d, e = (x.cpu().numpy() for x in out)
+    d, e = (x.cpu().numpy() for x in out[2:])
     t0 = time.perf_counter()
-    vo, to, do, eo = oracle.bulge_chase(W)
+    _, _, do, eo = oracle.bulge_chase(W)
     cpu_s = time.perf_counter() - t0
-    K = len(tau)
+    K = int(out[1].numel())
     # real flops of the reduction, counted from the store: a reflector of length L is applied from the
     # right to the L x b block below its diagonal block and from the left to the b columns beside it
     # (4 L b each) and two-sidedly to its L x L diagonal block (4 L^2); a complex flop counts 4
@@ -156,8 +172,7 @@ def bulge_bench(args):
                      "kernel": "tbbt::bc::bulge_kernel", "note": "latency-bound: a chain of dependent sweeps"},
         "cpu_baseline": {"value": cpu_s * 1e3, "unit": "ms", "cores": 1, "kind": "oracle",
                          "sample": "the whole reduction, single-threaded C"},
-        "parity": {"max_abs_d": float(np.abs(d - do).max()), "max_abs_e": float(np.abs(e - eo).max(initial=0)),
-                   "max_abs_tau": float(np.abs(tau - to).max(initial=0)), "max_abs_v": float(np.abs(v - vo).max(initial=0))},
+        "parity": bulge_parity(d, e, do, eo),
         "speedup_vs_cpu_oracle": cpu_s * 1e3 / ms, "gpu_launches": 3 * args.steps, "clocks": clocks.summary(),
     }
     print(json.dumps(line), flush=True)
