@@ -21,6 +21,13 @@ their pins (the tests that tie them to something other than themselves):
   reflector products, residual ||BZ - Z Lambda|| and orthogonality of the
   whole chain, unitary invariance of column norms; planted mistakes (forward
   order, conjugation dropped, shifted rows) fail these.
+* ``full_to_band``: Eq. 6a -- LAPACK's tridiagonalisation (?sytrd / ?hetrd,
+  lower) at b = 1, spectrum of B equal to LAPACK's on the dense matrix,
+  reconstruction A = Q1 B Q1^H with the back-transformation below.
+* ``back_transform_full``: Eq. 6e -- the same reconstruction, unitarity of
+  Q1, explicit dense reflector products, the identity on the first b rows,
+  and the residual and orthogonality of the whole two-stage chain
+  (6a -> 6b -> 6c -> 6d -> 6e) on the dense matrix.
 """
 
 from __future__ import annotations
@@ -111,6 +118,13 @@ def _configure(L):
         g = getattr(L, f"orc_back_transform_{s}")
         g.restype = ctypes.c_int
         g.argtypes = [i64, i64, i64, p, p, p, i64, ctypes.c_int]
+    for s in ("d", "z"):
+        f = getattr(L, f"orc_full_to_band_{s}")
+        f.restype = i64
+        f.argtypes = [i64, i64, p, i64, p]
+        g = getattr(L, f"orc_back_transform_full_{s}")
+        g.restype = ctypes.c_int
+        g.argtypes = [i64, i64, i64, p, i64, p, p, i64, ctypes.c_int]
     L.orc_tridiag_ql.restype = ctypes.c_int
     L.orc_tridiag_ql.argtypes = [i64, p, p, p, i64]
     L.orc_jacobi.restype = ctypes.c_int
@@ -251,4 +265,55 @@ def back_transform(hh_v: np.ndarray, hh_tau: np.ndarray, n: int, b: int, q: np.n
     rc = fn(n, b, nev, _ptr(v), _ptr(t), _ptr(q), max(ldq, 1), int(nthreads))
     if rc != 0:
         raise RuntimeError("oracle back-transform failed")
+    return q
+
+
+# --------------------------------------------------------------------------
+# Eq. 6a: full -> band, and Eq. 6e: band -> full back-transformation
+# --------------------------------------------------------------------------
+
+def num_full_reflectors(n: int, b: int) -> int:
+    """Reflectors of the full -> band reduction: one per column c = 0..n-b-1."""
+    return max(n - b, 0)
+
+
+def full_to_band(A: np.ndarray, b: int):
+    """Reduce the dense symmetric/Hermitian ``A`` (n x n, both triangles) to
+    a band matrix of semi-bandwidth ``b``. Returns ``(a, tau)``: ``a``
+    (Fortran order) holds the band of B in |i-j| <= b and the reflector of
+    column c below it (v[0] = 1 implicit at row c+b, v[1:] in
+    ``a[c+b+1:, c]``); ``tau`` has max(n-b, 0) entries."""
+    cplx = np.iscomplexobj(A)
+    dt = np.complex128 if cplx else np.float64
+    n = A.shape[0]
+    a = np.asfortranarray(np.array(A, dtype=dt))
+    tau = np.zeros(max(n - b, 1), dt)
+    fn = lib().orc_full_to_band_z if cplx else lib().orc_full_to_band_d
+    k = fn(n, b, _ptr(a), max(n, 1), _ptr(tau))
+    assert k == num_full_reflectors(n, b)
+    return a, tau[: num_full_reflectors(n, b)]
+
+
+def band_of(a: np.ndarray, b: int) -> np.ndarray:
+    """The dense band matrix B held in the |i-j| <= b entries of ``a``."""
+    n = a.shape[0]
+    i, j = np.indices((n, n))
+    return np.where(np.abs(i - j) <= b, a, 0)
+
+
+def back_transform_full(a: np.ndarray, tau: np.ndarray, n: int, b: int, q: np.ndarray, nthreads: int = 1):
+    """Apply Q1 = H_0 ... H_{n-b-1} (the reflectors held below the band of
+    ``a``) to the columns of ``q`` (shape (ldq, nev), Fortran order), last
+    reflector first, in place. Returns ``q``."""
+    cplx = np.iscomplexobj(q)
+    dt = np.complex128 if cplx else np.float64
+    assert q.dtype == dt and q.flags.f_contiguous
+    ldq, nev = q.shape
+    a = np.asfortranarray(a, dtype=dt)
+    t = np.ascontiguousarray(tau, dtype=dt)
+    assert t.size >= num_full_reflectors(n, b) and a.shape[0] >= n
+    fn = lib().orc_back_transform_full_z if cplx else lib().orc_back_transform_full_d
+    rc = fn(n, b, nev, _ptr(a), max(a.shape[0], 1), _ptr(t), _ptr(q), max(ldq, 1), int(nthreads))
+    if rc != 0:
+        raise RuntimeError("oracle band -> full back-transform failed")
     return q

@@ -1,6 +1,8 @@
 /*
- * CPU oracle for the tridiagonal -> band eigenvector back-transformation of
- * the two-stage symmetric / Hermitian eigensolver (arXiv 2002.10991, Eq. 6).
+ * CPU oracle for the eigenvector back-transformations of the two-stage
+ * symmetric / Hermitian eigensolver (arXiv 2002.10991, Eq. 6): tridiagonal
+ * -> band (Eq. 6d) and band -> full (Eq. 6e), with the reductions that
+ * produce their reflectors.
  *
  * TEST INFRASTRUCTURE ONLY. Plain, slow, obviously correct C in double
  * precision. Only the tests, the smoke check and the CPU-baseline leg of the
@@ -12,6 +14,8 @@
  *   orc_bulge_chase_{d,z}                     band -> tridiagonal (Eq. 6b)
  *   orc_tridiag_ql                            T X = X Sigma (Eq. 6c), implicit QL
  *   orc_back_transform_{d,z}                  Z = Q^* X (Eq. 6d / Eq. 8)
+ *   orc_full_to_band_{d,z}                    full -> band (Eq. 6a)
+ *   orc_back_transform_full_{d,z}             C = P^* Y (Eq. 6e)
  *   orc_jacobi                                brute-force dense eigensolver
  */
 #define _GNU_SOURCE

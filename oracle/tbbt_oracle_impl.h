@@ -237,6 +237,140 @@ int FN(orc_back_transform_)(int64_t n, int64_t b, int64_t nev, const SCALAR *hh_
   return rc;
 }
 
+/*
+ * Full -> band reduction, Eq. 6a (B = P H P^*, Sec. 2.1, Fig. 1), written as
+ * its definition: for every column c = 0 .. n-b-1 in turn, one reflector
+ * from the column's entries below the band, x = A[c+b : n, c], and the
+ * two-sided update A <- H^H A H on the whole dense Hermitian matrix. (A
+ * blocked panel algorithm computes the same reflectors: a reflector of
+ * column c acts on rows and columns >= c+b, so it never touches the columns
+ * of its own panel.) P^* = Q1 = H_0 H_1 ... H_{n-b-1}.
+ *
+ * a:   in, the full Hermitian matrix (both triangles), n x n column-major.
+ *      out, LAPACK-style: entries with |i - j| <= b hold the band matrix B
+ *      (the upper triangle the conjugate of the lower), the reflector of column c has v[0] = 1 at row c+b
+ *      (implicit) and v[1:] in a[c+b+1 : n, c], the rest of the strictly
+ *      upper triangle is zero.
+ * tau: out, max(n-b, 0) entries (a length-1 reflector of a real matrix has
+ *      tau = 0; of a Hermitian one it makes B[c+b, c] real).
+ * Returns the number of reflectors, max(n-b, 0).
+ */
+int64_t FN(orc_full_to_band_)(int64_t n, int64_t b, SCALAR *a, int64_t lda, SCALAR *tau) {
+  int64_t K1 = n > b ? n - b : 0;
+  SCALAR *A = (SCALAR *)malloc(sizeof(SCALAR) * (size_t)(n > 0 ? n * n : 1));
+  SCALAR *V = (SCALAR *)calloc((size_t)(n > 0 ? n * n : 1), sizeof(SCALAR));
+  SCALAR *x = (SCALAR *)malloc(sizeof(SCALAR) * (size_t)(n > 0 ? n : 1));
+  SCALAR *v = (SCALAR *)malloc(sizeof(SCALAR) * (size_t)(n > 0 ? n : 1));
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < n; ++i) A[i + j * n] = a[i + j * lda];
+  for (int64_t c = 0; c < K1; ++c) {
+    int64_t r = c + b, L = n - r;
+    for (int64_t t = 0; t < L; ++t) x[t] = A[r + t + c * n];
+    SCALAR tk;
+    double beta;
+    FN(house)(L, x, v, &tk, &beta);
+    /* left: rows [r, n) of every column, A <- H^H A */
+    for (int64_t j = 0; j < n; ++j) {
+      SCALAR w = 0.0;
+      for (int64_t t = 0; t < L; ++t) w += CONJ(v[t]) * A[r + t + j * n];
+      for (int64_t t = 0; t < L; ++t) A[r + t + j * n] -= CONJ(tk) * v[t] * w;
+    }
+    /* right: columns [r, n) of every row, A <- A H */
+    for (int64_t i = 0; i < n; ++i) {
+      SCALAR w = 0.0;
+      for (int64_t t = 0; t < L; ++t) w += A[i + (r + t) * n] * v[t];
+      for (int64_t t = 0; t < L; ++t) A[i + (r + t) * n] -= tk * w * CONJ(v[t]);
+    }
+    /* column c is beta e_1 below the band, row c its conjugate, exactly */
+    A[r + c * n] = beta;
+    A[c + r * n] = beta;
+    for (int64_t t = 1; t < L; ++t) {
+      A[r + t + c * n] = 0.0;
+      A[c + (r + t) * n] = 0.0;
+    }
+    for (int64_t t = 1; t < L; ++t) V[r + t + c * n] = v[t];
+    tau[c] = tk;
+  }
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < n; ++i) {
+      int64_t dlt = i - j;
+      if (dlt >= 0 && dlt <= b) /* the lower band; the upper one mirrors it */
+        a[i + j * lda] = (i == j) ? RE(A[i + j * n]) : A[i + j * n];
+      else if (dlt < 0 && -dlt <= b)
+        a[i + j * lda] = CONJ(A[j + i * n]);
+      else if (dlt > b)
+        a[i + j * lda] = V[i + j * n];
+      else
+        a[i + j * lda] = 0.0;
+    }
+  free(A);
+  free(V);
+  free(x);
+  free(v);
+  return K1;
+}
+
+/*
+ * Band -> full back-transformation of eigenvectors, Eq. 6e:
+ * C = P^* Y = H_0 H_1 ... H_{K1-1} Y with the reflectors of the full -> band
+ * reduction in the layout written by orc_full_to_band (reflector c: v[0] = 1
+ * at row c+b, v[1:] = a[c+b+1 : n, c], tau[c]), each applied as in Eq. 8,
+ * y <- y - tau v (v^H y), last reflector first. Threads take column blocks.
+ */
+typedef struct {
+  int64_t n, b, K1, c0, c1, lda, ldq;
+  const SCALAR *a;
+  const SCALAR *tau;
+  SCALAR *q;
+} FN(bf_job_t);
+
+static void *FN(bf_worker)(void *arg) {
+  FN(bf_job_t) *J = (FN(bf_job_t) *)arg;
+  for (int64_t k = J->K1 - 1; k >= 0; --k) {
+    int64_t r = k + J->b, L = J->n - r;
+    const SCALAR *tail = J->a + k * J->lda + r + 1; /* v[1:] */
+    SCALAR tk = J->tau[k];
+    for (int64_t c = J->c0; c < J->c1; ++c) {
+      SCALAR *y = J->q + c * J->ldq + r;
+      SCALAR w = y[0];
+      for (int64_t t = 1; t < L; ++t) w += CONJ(tail[t - 1]) * y[t];
+      SCALAR tw = tk * w;
+      y[0] -= tw;
+      for (int64_t t = 1; t < L; ++t) y[t] -= tw * tail[t - 1];
+    }
+  }
+  return NULL;
+}
+
+int FN(orc_back_transform_full_)(int64_t n, int64_t b, int64_t nev, const SCALAR *a, int64_t lda,
+                                 const SCALAR *tau, SCALAR *q, int64_t ldq, int nthreads) {
+  int64_t K1 = n > b ? n - b : 0;
+  if (nthreads < 1) nthreads = 1;
+  if (nthreads > nev) nthreads = (int)(nev > 0 ? nev : 1);
+  FN(bf_job_t) *jobs = (FN(bf_job_t) *)calloc((size_t)nthreads, sizeof(FN(bf_job_t)));
+  pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+  for (int t = 0; t < nthreads; ++t) {
+    jobs[t].n = n;
+    jobs[t].b = b;
+    jobs[t].K1 = K1;
+    jobs[t].c0 = nev * t / nthreads;
+    jobs[t].c1 = nev * (t + 1) / nthreads;
+    jobs[t].lda = lda;
+    jobs[t].ldq = ldq;
+    jobs[t].a = a;
+    jobs[t].tau = tau;
+    jobs[t].q = q;
+  }
+  int rc = 0;
+  for (int t = 1; t < nthreads; ++t)
+    if (pthread_create(&th[t], NULL, FN(bf_worker), &jobs[t]) != 0) rc = -1;
+  FN(bf_worker)(&jobs[0]);
+  for (int t = 1; t < nthreads; ++t) pthread_join(th[t], NULL);
+  free(jobs);
+  free(th);
+  return rc;
+}
+
 #undef FN
 #undef CAT
 #undef CAT_
