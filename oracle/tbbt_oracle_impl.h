@@ -334,9 +334,9 @@ static void *FN(bf_worker)(void *arg) {
       SCALAR *y = J->q + c * J->ldq + r;
       SCALAR w = y[0];
       for (int64_t t = 1; t < L; ++t) w += CONJ(tail[t - 1]) * y[t];
-      SCALAR tw = tk * w;
-      y[0] -= tw;
-      for (int64_t t = 1; t < L; ++t) y[t] -= tw * tail[t - 1];
+      SCALAR tauw = tk * w;
+      y[0] -= tauw;
+      for (int64_t t = 1; t < L; ++t) y[t] -= tauw * tail[t - 1];
     }
   }
   return NULL;

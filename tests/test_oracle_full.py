@@ -134,7 +134,7 @@ MUTATIONS = {
     "full_dot_without_conj": [("tbbt_oracle_impl.h", "w += CONJ(tail[t - 1]) * y[t];", "w += tail[t - 1] * y[t];")],
     "full_rows_shifted": [("tbbt_oracle_impl.h", "int64_t r = k + J->b, L = J->n - r;",
                            "int64_t r = k + J->b - 1, L = J->n - r;")],
-    "full_unit_entry_dropped": [("tbbt_oracle_impl.h", "    y[0] -= tw;\n", "\n")],
+    "full_unit_entry_dropped": [("tbbt_oracle_impl.h", "    y[0] -= tauw;\n", "\n")],
     "reduction_right_update_conj_tau": [("tbbt_oracle_impl.h", "A[i + (r + t) * n] -= tk * w * CONJ(v[t]);",
                                          "A[i + (r + t) * n] -= CONJ(tk) * w * CONJ(v[t]);")],
     "reduction_column_offset": [("tbbt_oracle_impl.h", "for (int64_t t = 0; t < L; ++t) x[t] = A[r + t + c * n];",
