@@ -102,11 +102,83 @@ BULGE_WORKLOADS = {"bulge-real-n4096-b64": (4096, 64, False), "bulge-complex-n40
                    "bulge-real-n8192-b64": (8192, 64, False)}
 
 
+# band -> full back-transformation (the step after the path): (n, b, nev, complex, seed)
+B2F_WORKLOADS = {"b2f-real-n8192-b64-nev4096": (8192, 64, 4096, False, I.SEED_BASE + 8),
+                 "b2f-complex-n4096-b64-nev2048": (4096, 64, 2048, True, I.SEED_BASE + 10),
+                 "b2f-real-n4096-b64-nev2048": (4096, 64, 2048, False, I.SEED_BASE + 11)}
+
+
 def set_workload(name: str):
     global WORKLOAD
-    if name not in I.WORKLOADS and name != BATCH_WORKLOAD and name not in BULGE_WORKLOADS:
+    if name not in I.WORKLOADS and name != BATCH_WORKLOAD and name not in BULGE_WORKLOADS and \
+            name not in B2F_WORKLOADS:
         raise SystemExit(f"unknown workload {name}")
     WORKLOAD = name
+
+
+def b2f_bench(args):
+    """Band -> full back-transformation (Eq. 6e) on the GPU: one call of the
+    C ABI per step (T factors of the 32-reflector blocks, then the apply
+    kernel), timed with CUDA events on the calling stream; the oracle on the
+    host cores on a column sample; parity on sampled columns."""
+    import torch
+
+    import oracle
+    import paper_2002_10991_gb300 as P
+
+    torch.cuda.set_device(0)
+    n, b, nev, cplx, seed = B2F_WORKLOADS[WORKLOAD]
+    a, tau = I.synthetic_full_store(n, b, seed, cplx)
+    Y = I.eigvec_block(n, nev, seed + 1, cplx)
+    da = torch.from_numpy(np.ascontiguousarray(a.T)).cuda().t()
+    dt = torch.from_numpy(tau).cuda()
+    dq = torch.from_numpy(np.ascontiguousarray(Y.T)).cuda().t()
+    cols = np.unique(np.linspace(0, nev - 1, 8).astype(int))
+    P.trans_ev_band_to_full(da, dt, n, b, nev, dq)  # parity pass on the original columns
+    P.stream_check()
+    Cg = dq[:, torch.from_numpy(cols).cuda()].cpu().numpy()
+    Co = oracle.back_transform_full(a, tau, n, b, np.asfortranarray(Y[:, cols]), nthreads=oracle.num_cpus())
+    err = float(np.abs(Cg - Co).max())
+    for _ in range(max(args.warmup, 1)):
+        P.trans_ev_band_to_full(da, dt, n, b, nev, dq)
+    P.stream_check()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clocks:
+        e0.record(stream)
+        for _ in range(args.steps):
+            P.trans_ev_band_to_full(da, dt, n, b, nev, dq)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    P.stream_check()
+    ms = e0.elapsed_time(e1) / args.steps
+    K1 = max(n - b, 0)
+    sum_l = K1 * (K1 + 1) // 2  # reflector c has length n - c - b
+    flops = (16.0 if cplx else 4.0) * nev * sum_l
+    tflops = flops / (ms * 1e-3) / 1e12
+    # the oracle on the host cores, on a column sample sized to ~10 s
+    cores = oracle.num_cpus()
+    ncs = max(cores, 16)
+    Ys = np.asfortranarray(Y[:, :ncs])
+    t0 = time.perf_counter()
+    oracle.back_transform_full(a, tau, n, b, Ys, nthreads=cores)
+    cpu_s = time.perf_counter() - t0
+    cpu_tf = (16.0 if cplx else 4.0) * ncs * sum_l / cpu_s / 1e12
+    line = {
+        "metric": "band->full back-transform TFLOP/s (Eq. 6e)", "value": tflops, "unit": "TFLOP/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128" if cplx else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "nbw": b, "nev": nev, "reflectors": K1,
+                   "store": "seeded unitary reflectors, LAPACK layout", "l2": "inputs larger than L2"},
+        "roofline": {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "tbbt::bf::bf_apply_kernel (timed with the T-factor kernel: the whole call)"},
+        "cpu_baseline": {"value": cpu_tf, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{ncs} of {nev} columns"},
+        "parity": {"max_abs_err_vs_oracle": err, "columns": len(cols)},
+        "gpu_launches": 2 * args.steps, "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
 
 
 def bulge_parity(d, e, do, eo):
@@ -431,7 +503,8 @@ def main():
                          "split-precision form on the same inputs (0: skip)")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="named workload (default: the benchmark workload; others are for profiler captures, "
-                         "the batched-form measurement and the GPU bulge chase: " + ", ".join(BULGE_WORKLOADS) + ")")
+                         "the batched-form measurement, the GPU bulge chase (" + ", ".join(BULGE_WORKLOADS) + ") and the band -> full "
+                         "back-transformation (" + ", ".join(B2F_WORKLOADS) + "))")
     ap.add_argument("--autotune", action="store_true", help="batched workload: tune the launch geometry first")
     ap.add_argument("--variant", default="fp64", choices=list(VARIANTS),
                     help="fp64: reflector-by-reflector FP64 kernel; split: WY blocks on BF16 tensor cores "
@@ -445,6 +518,9 @@ def main():
         return
     if WORKLOAD in BULGE_WORKLOADS:
         bulge_bench(args)
+        return
+    if WORKLOAD in B2F_WORKLOADS:
+        b2f_bench(args)
         return
     world, rank, local = dist_setup()
 

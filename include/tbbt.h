@@ -294,6 +294,32 @@ tbbt_status tbbt_bulge_chase_d(const double *band, int64_t ldb, int64_t n, int64
 tbbt_status tbbt_bulge_chase_z(const void *band, int64_t ldb, int64_t n, int64_t nbw, void *hh_v, void *hh_tau,
                                double *d, double *e, void *stream);
 
+/* -------------------------------------------------------------------------
+ * Band -> full back-transformation of eigenvectors (Eq. 6e, Sec. 2.1):
+ * C = P^* Y = Q1 Y, Q1 = H_0 H_1 ... H_{K1-1}, K1 = max(n - nbw, 0), the
+ * reflectors of the full -> band reduction (Eq. 6a). Reflector c acts on rows
+ * c+nbw .. n-1: H_c = I - tau[c] v_c v_c^H with v_c[c+nbw] = 1 (not stored)
+ * and v_c[c+nbw+1 : n] = a[c+nbw+1 : n, c] (LAPACK layout: the reflectors sit
+ * below the band of the reduced matrix; entries at or above the nbw-th
+ * sub-diagonal are not read).
+ *
+ * a:    device, n x n column-major, lda >= max(1, n); read only.
+ * tau:  device, K1 entries; read only.
+ * q:    device, n x nev column-major, ldq >= max(1, n); in: Y (the
+ *       eigenvectors of the band matrix, e.g. the output of
+ *       tbbt_trans_ev_tridi_to_band_*), out: C. Columns are independent.
+ * Complex variant: a, tau and q are interleaved complex128.
+ * Runs on `stream` (NULL: the legacy default stream) without host
+ * synchronisation; allocates and frees a P x 32 x 32 workspace of T factors
+ * stream-ordered (P = ceil(K1/32)). Any nbw >= 1; nbw >= n is a no-op.
+ * Errors: TBBT_EINVAL for n < 0, nbw < 1, nev outside [0, n], small lda/ldq,
+ * null or misaligned pointers when there is work; TBBT_ENOMEM, TBBT_ECUDA.
+ * ------------------------------------------------------------------------- */
+tbbt_status tbbt_trans_ev_band_to_full_d(const double *a, int64_t lda, const double *tau, int64_t n, int64_t nbw,
+                                         int64_t nev, double *q, int64_t ldq, void *stream);
+tbbt_status tbbt_trans_ev_band_to_full_z(const void *a, int64_t lda, const void *tau, int64_t n, int64_t nbw,
+                                         int64_t nev, void *q, int64_t ldq, void *stream);
+
 /* Host-side check of the block schedule (no GPU needed): largest number of
  * rows a thread block ever holds at once for these parameters, or -1 if the
  * schedule would touch a row twice in one step. Used by tests to show the

@@ -96,6 +96,10 @@ def load():
             f = getattr(L, name)
             f.restype = c_int
             f.argtypes = [p, i64, i64, i64, p, p, p, p, p]
+        for name in ("tbbt_trans_ev_band_to_full_d", "tbbt_trans_ev_band_to_full_z"):
+            f = getattr(L, name)
+            f.restype = c_int
+            f.argtypes = [p, i64, p, i64, i64, i64, p, i64, p]
         L.tbbt_schedule_max_live_rows.restype = i64
         L.tbbt_schedule_max_live_rows.argtypes = [i64, i64, c_int, i32, i32]
         _lib = L

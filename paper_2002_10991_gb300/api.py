@@ -118,6 +118,28 @@ def bulge_chase(band, nbw: int | None = None, stream=None):
     return hh_v, hh_tau, d, e
 
 
+def trans_ev_band_to_full(a, tau, n: int, nbw: int, nev: int, q, stream=None):
+    """Eq. 6e on device tensors: q[:n, :nev] <- H_0 ... H_{n-nbw-1} q[:n, :nev]
+    with the full -> band reflectors held LAPACK-style below the band of
+    ``a`` (n x n, column-major; reflector c has v[0] = 1 at row c+nbw and
+    v[1:] in a[c+nbw+1:, c]) and ``tau`` (n-nbw entries). float64 or
+    complex128 CUDA tensors; q column-major."""
+    cplx = _is_complex_dtype(q)
+    if a.dim() != 2 or a.shape[0] < n or (a.shape[1] > 1 and a.stride(0) != 1):
+        raise ValueError("a must be a column-major 2-D tensor with at least n rows")
+    lda = a.stride(1) if a.shape[1] > 1 else max(a.shape[0], 1)
+    ldq, _ = _q_layout(q, n)
+    L = _native.load()
+    f = L.tbbt_trans_ev_band_to_full_z if cplx else L.tbbt_trans_ev_band_to_full_d
+
+    def ptr(t):
+        return ctypes.c_void_p(t.data_ptr() if t.numel() else 0)
+
+    st = f(ptr(a), lda, ptr(tau), n, nbw, nev, ptr(q), ldq, _stream_handle(stream))
+    _check(st, "tbbt_trans_ev_band_to_full")
+    return q
+
+
 def trans_ev_tridi_to_band_host(hh_v, hh_tau, n: int, nbw: int, nev: int, q, ldq: int | None = None, stream=None,
                                 synchronize: bool = True):
     """The same with every array in host memory (numpy arrays or CPU

@@ -1,0 +1,277 @@
+// Band -> full back-transformation of eigenvectors (Eq. 6e, Sec. 2.1):
+// C = P^* Y = Q1 Y with Q1 = H_0 H_1 ... H_{K1-1} the reflectors of the
+// full -> band reduction (Eq. 6a), one per column c = 0 .. n-b-1, acting on
+// rows c+b .. n-1.
+//
+// Reflector store (LAPACK layout, as the full -> band step leaves it): the
+// n x n column-major matrix `a` holds reflector c's v[0] = 1 implicitly at
+// row c+b and v[1:] in a[c+b+1 : n, c]; tau[c]. Entries at or above the b-th
+// sub-diagonal are not read.
+//
+// Unlike Eq. 6d (short reflectors on a sliding window) this step is dense:
+// 32 consecutive reflectors form one WY block H_{c0} ... H_{c0+31} =
+// I - V T V^H (V staircase, T upper triangular, built by the forward
+// recurrence in FP64). Blocks are applied last-first. FP64 on GB300 runs at
+// 2 DFMA per clock per SM, two orders of magnitude below shared-memory and
+// L2 rates, so the kernel is FP64-pipe bound once the pipe is kept fed:
+//   * one thread block per strip of <= 32 columns of Y, grid sized to the
+//     SMs x resident blocks, applies every block to its strip;
+//   * one pass over the rows per block boundary: the rows of a 64-row chunk
+//     (32 for complex) get the update of block p+1, Y -= V_{p+1} W_{p+1},
+//     and then feed W_p += V_p^H Y of the next block, so Y is read and
+//     written once per block, not three times;
+//   * the next chunk's Y and V are loaded into registers while the current
+//     chunk is computed.
+#pragma once
+
+#include <stdint.h>
+
+namespace tbbt {
+namespace bf {
+
+constexpr int NB = 32;        // reflectors per WY block
+constexpr int THREADS = 256;  // threads per block
+constexpr int WMAX = 32;      // columns per strip at most
+constexpr int PADT = NB + 1;  // padded row length of t-major tiles
+
+template <typename T>
+struct Ops;
+
+template <>
+struct Ops<double> {
+  static __device__ __forceinline__ double zero() { return 0.0; }
+  static __device__ __forceinline__ double one() { return 1.0; }
+  static __device__ __forceinline__ void mac(double &s, double x, double y) { s = fma(x, y, s); }
+  static __device__ __forceinline__ void macc(double &s, double x, double y) { s = fma(x, y, s); }  // conj(x) y
+  static __device__ __forceinline__ void msub(double &s, double x, double y) { s = fma(-x, y, s); }
+  static __device__ __forceinline__ double neg_mul(double x, double y) { return -(x * y); }
+  static __device__ __forceinline__ double ldro(const double *p) { return __ldg(p); }
+};
+
+template <>
+struct Ops<zdouble> {
+  static __device__ __forceinline__ zdouble zero() { return zdouble{0.0, 0.0}; }
+  static __device__ __forceinline__ zdouble one() { return zdouble{1.0, 0.0}; }
+  static __device__ __forceinline__ void mac(zdouble &s, zdouble x, zdouble y) {
+    s.re = fma(x.re, y.re, s.re);
+    s.re = fma(-x.im, y.im, s.re);
+    s.im = fma(x.re, y.im, s.im);
+    s.im = fma(x.im, y.re, s.im);
+  }
+  static __device__ __forceinline__ void macc(zdouble &s, zdouble x, zdouble y) {
+    s.re = fma(x.re, y.re, s.re);
+    s.re = fma(x.im, y.im, s.re);
+    s.im = fma(x.re, y.im, s.im);
+    s.im = fma(-x.im, y.re, s.im);
+  }
+  static __device__ __forceinline__ void msub(zdouble &s, zdouble x, zdouble y) {
+    s.re = fma(-x.re, y.re, s.re);
+    s.re = fma(x.im, y.im, s.re);
+    s.im = fma(-x.re, y.im, s.im);
+    s.im = fma(-x.im, y.re, s.im);
+  }
+  static __device__ __forceinline__ zdouble neg_mul(zdouble x, zdouble y) {
+    return zdouble{-(x.re * y.re - x.im * y.im), -(x.re * y.im + x.im * y.re)};
+  }
+  static __device__ __forceinline__ zdouble ldro(const zdouble *p) {
+    const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+    return zdouble{v.x, v.y};
+  }
+};
+
+struct Geo {
+  const void *a;
+  int64_t lda;
+  const void *tau;
+  int32_t n, b, K1, P;  // P = ceil(K1 / NB) blocks
+};
+
+// Entry (r, t) of the staircase V of block p: reflector c = NB p + t.
+template <typename T>
+__device__ __forceinline__ T vget(const Geo &g, int32_t r, int32_t p, int32_t t) {
+  const int32_t c = NB * p + t;
+  if (c >= g.K1 || r >= g.n) return Ops<T>::zero();
+  const int32_t rr = r - (c + g.b);
+  if (rr < 0) return Ops<T>::zero();
+  if (rr == 0) return Ops<T>::one();
+  return Ops<T>::ldro(reinterpret_cast<const T *>(g.a) + (int64_t)c * g.lda + r);
+}
+
+// T factor of every block (one thread block each): G = V^H V over the
+// block's rows, then T_kk = tau_k, T[0:k, k] = -tau_k T[0:k, 0:k] G[0:k, k]
+// (the forward recurrence of the WY representation). Tws: P x NB x NB,
+// column-major per block.
+template <typename T>
+__global__ void __launch_bounds__(THREADS) bf_tfactor_kernel(Geo g, T *__restrict__ Tws) {
+  constexpr int RC = sizeof(T) == 16 ? 32 : 64;  // static shared memory stays below 48 KB
+  __shared__ T Vs[RC][PADT];
+  __shared__ T Gs[NB][PADT];
+  T(*Ts)[PADT] = Vs;  // the T factor reuses the V tile once G is complete
+  const int p = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int k = tid % NB, l0 = tid / NB;  // owns G[k][l0 + 8 i]
+  T acc[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) acc[i] = Ops<T>::zero();
+  const int32_t rs = NB * p + g.b;
+  for (int32_t r0 = rs; r0 < g.n; r0 += RC) {
+#pragma unroll
+    for (int i = 0; i < RC * NB / THREADS; ++i) {
+      const int e = tid + THREADS * i;
+      const int r = e % RC, t = e / RC;
+      Vs[r][t] = vget<T>(g, r0 + r, p, t);
+    }
+    __syncthreads();
+    for (int r = 0; r < RC; ++r) {
+      const T vk = Vs[r][k];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) Ops<T>::macc(acc[i], vk, Vs[r][l0 + 8 * i]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) Gs[k][l0 + 8 * i] = acc[i];  // G[k][l] = v_k^H v_l
+  __syncthreads();
+  if (tid < NB) {
+    const int i = tid;
+    const T *tau = reinterpret_cast<const T *>(g.tau);
+    for (int kk = 0; kk < NB; ++kk) {
+      const int32_t c = NB * p + kk;
+      const T tk = c < g.K1 ? tau[c] : Ops<T>::zero();
+      T val = Ops<T>::zero();
+      if (i < kk) {
+        T s = Ops<T>::zero();
+        for (int l = i; l < kk; ++l) Ops<T>::mac(s, Ts[i][l], Gs[l][kk]);
+        val = Ops<T>::neg_mul(tk, s);
+      } else if (i == kk) {
+        val = tk;
+      }
+      Ts[i][kk] = val;
+      __syncwarp();
+    }
+    for (int kk = 0; kk < NB; ++kk) Tws[(int64_t)p * NB * NB + i + NB * kk] = Ts[i][kk];
+  }
+}
+
+struct ApplyArgs {
+  Geo g;
+  const void *Tws;
+  void *q;
+  int64_t ldq;
+  int32_t nev, grid;
+};
+
+template <typename T, int RC>
+struct Smem {
+  T Zs[WMAX][RC];    // Y chunk, column-major
+  T Vu[NB][RC];      // V of the updating block, t-major
+  T Va[RC][PADT];    // V of the accumulating block, r-major
+  T Wu[NB][PADT];    // T_u V_u^H Y of the updating block
+  T Wt[NB][PADT];    // V_a^H Y of the accumulating block, before T
+  T Ts[NB][PADT];    // T of the accumulating block
+};
+
+template <typename T, int RC>
+__global__ void __launch_bounds__(THREADS, 2) bf_apply_kernel(ApplyArgs A) {
+  constexpr int NCG = THREADS / RC;   // column groups of the update
+  constexpr int MAXU = WMAX / NCG;    // update columns per thread
+  constexpr int NLD = RC * WMAX / THREADS;  // loaded elements per thread per tile
+  static_assert(RC * NB == RC * WMAX, "V and Y tiles have the same shape");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem<T, RC> &S = *reinterpret_cast<Smem<T, RC> *>(smem_raw);
+  const Geo &g = A.g;
+  const int tid = threadIdx.x;
+  const int32_t j0 = (int32_t)((int64_t)A.nev * blockIdx.x / A.grid);
+  const int32_t w = (int32_t)((int64_t)A.nev * (blockIdx.x + 1) / A.grid) - j0;
+  T *__restrict__ q = reinterpret_cast<T *>(A.q) + (int64_t)j0 * A.ldq;
+  const T *__restrict__ Tws = reinterpret_cast<const T *>(A.Tws);
+
+  const int ur = tid % RC, ucg = tid / RC;  // update: row, column group
+  const int nu = (w - ucg + NCG - 1) / NCG;
+  const int at = tid % NB, acg = tid / NB;  // accumulate: reflector, column group (8 groups)
+  const int na = (w - acg + 7) / 8;
+
+  T zr[NLD], vur[NLD], var[NLD];
+  auto load = [&](int32_t r0, int pu, int pa) {
+#pragma unroll
+    for (int i = 0; i < NLD; ++i) {
+      const int e = tid + THREADS * i;
+      const int r = e % RC, c = e / RC;
+      const int32_t row = r0 + r;
+      zr[i] = (c < w && row < g.n) ? q[(int64_t)c * A.ldq + row] : Ops<T>::zero();
+      vur[i] = pu >= 0 ? vget<T>(g, row, pu, c) : Ops<T>::zero();
+      var[i] = pa >= 0 ? vget<T>(g, row, pa, c) : Ops<T>::zero();
+    }
+  };
+
+  for (int pa = g.P - 1; pa >= -1; --pa) {
+    const int pu = (pa + 1 <= g.P - 1) ? pa + 1 : -1;
+    const int32_t rs = NB * (pa >= 0 ? pa : pu) + g.b;
+    T wacc[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) wacc[i] = Ops<T>::zero();
+    load(rs, pu, pa);
+    for (int32_t r0 = rs; r0 < g.n; r0 += RC) {
+#pragma unroll
+      for (int i = 0; i < NLD; ++i) {
+        const int e = tid + THREADS * i;
+        const int r = e % RC, c = e / RC;
+        S.Zs[c][r] = zr[i];
+        S.Vu[c][r] = vur[i];
+        S.Va[r][c] = var[i];
+      }
+      __syncthreads();
+      if (r0 + RC < g.n) load(r0 + RC, pu, pa);
+      if (pu >= 0) {
+        T z[MAXU];
+#pragma unroll
+        for (int i = 0; i < MAXU; ++i)
+          if (i < nu) z[i] = S.Zs[ucg + NCG * i][ur];
+#pragma unroll 4
+        for (int t = 0; t < NB; ++t) {
+          const T vt = S.Vu[t][ur];
+#pragma unroll
+          for (int i = 0; i < MAXU; ++i)
+            if (i < nu) Ops<T>::msub(z[i], vt, S.Wu[t][ucg + NCG * i]);
+        }
+#pragma unroll
+        for (int i = 0; i < MAXU; ++i)
+          if (i < nu) {
+            S.Zs[ucg + NCG * i][ur] = z[i];
+            if (r0 + ur < g.n) q[(int64_t)(ucg + NCG * i) * A.ldq + r0 + ur] = z[i];
+          }
+      }
+      __syncthreads();
+      if (pa >= 0) {
+#pragma unroll 4
+        for (int r = 0; r < RC; ++r) {
+          const T vr = S.Va[r][at];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (i < na) Ops<T>::macc(wacc[i], vr, S.Zs[acg + 8 * i][r]);
+        }
+      }
+      __syncthreads();
+    }
+    if (pa >= 0) {
+      // W_a <- T_a (V_a^H Y): the next pass's update
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (i < na) S.Wt[at][acg + 8 * i] = wacc[i];
+      for (int e = tid; e < NB * NB; e += THREADS) S.Ts[e % NB][e / NB] = Tws[(int64_t)pa * NB * NB + e];
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (i < na) {
+          const int c = acg + 8 * i;
+          T s = Ops<T>::zero();
+          for (int l = at; l < NB; ++l) Ops<T>::mac(s, S.Ts[at][l], S.Wt[l][c]);
+          S.Wu[at][c] = s;
+        }
+      __syncthreads();
+    }
+  }
+}
+
+}  // namespace bf
+}  // namespace tbbt

@@ -19,6 +19,7 @@
 #include "split_kernels.cuh"
 #include "tc_split.cuh"
 #include "bulge.cuh"
+#include "b2f.cuh"
 
 using tbbt::StoreGeom;
 using tbbt::zdouble;
@@ -985,9 +986,80 @@ tbbt_status bulge_chase_impl(const T *band, int64_t ldb, int64_t n, int64_t nbw,
   cudaFreeAsync(progress, s);
   return rs;
 }
+// Band -> full back-transformation (Eq. 6e): T factors of the 32-reflector
+// blocks, then one pass per block boundary over every column strip.
+template <typename T>
+tbbt_status band_to_full_impl(const T *a, int64_t lda, const T *tau, int64_t n, int64_t nbw, int64_t nev, T *q,
+                              int64_t ldq, cudaStream_t s) {
+  if (n < 0 || n > (int64_t)1 << 30 || nbw < 1 || nev < 0 || nev > n) return TBBT_EINVAL;
+  if (lda < std::max<int64_t>(1, n) || ldq < std::max<int64_t>(1, n)) return TBBT_EINVAL;
+  const int64_t K1 = n > nbw ? n - nbw : 0;
+  if (K1 == 0 || nev == 0) return TBBT_OK;
+  if (!a || !tau || !q) return TBBT_EINVAL;
+  if (((uintptr_t)q | (uintptr_t)a | (uintptr_t)tau) % alignof(T) != 0) return TBBT_EINVAL;
+  constexpr int RC = sizeof(T) == 16 ? 32 : 64;
+  namespace bf = tbbt::bf;
+  const int32_t P = (int32_t)((K1 + bf::NB - 1) / bf::NB);
+  T *Tws = nullptr;
+  TBBT_CUDA_TRY(cudaMallocAsync((void **)&Tws, sizeof(T) * (size_t)P * bf::NB * bf::NB, s));
+  tbbt_status rs = TBBT_OK;
+  do {
+    bf::Geo g;
+    g.a = a;
+    g.lda = lda;
+    g.tau = tau;
+    g.n = (int32_t)n;
+    g.b = (int32_t)std::min<int64_t>(nbw, n);
+    g.K1 = (int32_t)K1;
+    g.P = P;
+    bf::bf_tfactor_kernel<T><<<P, bf::THREADS, 0, s>>>(g, Tws);
+    if (cudaGetLastError() != cudaSuccess) {
+      rs = TBBT_ECUDA;
+      break;
+    }
+    const size_t smem = sizeof(bf::Smem<T, RC>);
+    if (cudaFuncSetAttribute(bf::bf_apply_kernel<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+      rs = TBBT_ECUDA;
+      break;
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bf::bf_apply_kernel<T, RC>, bf::THREADS, smem) !=
+            cudaSuccess ||
+        per_sm < 1) {
+      rs = TBBT_ECUDA;
+      break;
+    }
+    // strips of <= 32 columns, as many as fit at once (balanced widths)
+    const int64_t slots = (int64_t)std::max(sms, 1) * per_sm;
+    const int64_t grid = std::max<int64_t>((nev + bf::WMAX - 1) / bf::WMAX, std::min<int64_t>(nev, slots));
+    bf::ApplyArgs A;
+    A.g = g;
+    A.Tws = Tws;
+    A.q = q;
+    A.ldq = ldq;
+    A.nev = (int32_t)nev;
+    A.grid = (int32_t)grid;
+    bf::bf_apply_kernel<T, RC><<<(unsigned)grid, bf::THREADS, smem, s>>>(A);
+    if (cudaGetLastError() != cudaSuccess) rs = TBBT_ECUDA;
+  } while (0);
+  cudaFreeAsync(Tws, s);
+  return rs;
+}
 }  // namespace
 
 extern "C" {
+tbbt_status tbbt_trans_ev_band_to_full_d(const double *a, int64_t lda, const double *tau, int64_t n, int64_t nbw,
+                                         int64_t nev, double *q, int64_t ldq, void *stream) {
+  return band_to_full_impl<double>(a, lda, tau, n, nbw, nev, q, ldq, (cudaStream_t)stream);
+}
+tbbt_status tbbt_trans_ev_band_to_full_z(const void *a, int64_t lda, const void *tau, int64_t n, int64_t nbw,
+                                         int64_t nev, void *q, int64_t ldq, void *stream) {
+  return band_to_full_impl<zdouble>((const zdouble *)a, lda, (const zdouble *)tau, n, nbw, nev, (zdouble *)q, ldq,
+                                    (cudaStream_t)stream);
+}
 tbbt_status tbbt_bulge_chase_d(const double *band, int64_t ldb, int64_t n, int64_t nbw, double *hh_v, double *hh_tau,
                                double *d, double *e, void *stream) {
   return bulge_chase_impl<double>(band, ldb, n, nbw, hh_v, hh_tau, d, e, (cudaStream_t)stream);

@@ -196,6 +196,32 @@ def synthetic_store(n: int, b: int, seed: int, complex_: bool = False):
     return np.ascontiguousarray(V.reshape(-1)), np.ascontiguousarray(tau.astype(dt))
 
 
+def synthetic_full_store(n: int, b: int, seed: int, complex_: bool = False):
+    """Random unitary reflectors in the layout the full -> band reduction
+    leaves (LAPACK style): ``a`` (n x n, Fortran order) holds reflector c's
+    v[1:] in ``a[c+b+1:, c]`` (v[0] = 1 implicit at row c+b) and N(0, 1)
+    values everywhere else, which the back-transformation must not read;
+    ``tau`` (max(n-b, 0) entries) makes each I - tau v v^H unitary, as in
+    ``synthetic_store``. Tails are N(0, 1/b) draws."""
+    dt = np.complex128 if complex_ else np.float64
+    a = normal(seed, 51, (n, n))
+    if complex_:
+        a = a + 1j * normal(seed, 52, (n, n))
+    a = np.asfortranarray(a.astype(dt).reshape(n, n).T)  # column c = draws c*n .. c*n+n-1
+    K1 = max(n - b, 0)
+    i = np.arange(n)[:, None]
+    c = np.arange(n)[None, :]
+    below = i > c + b
+    a[below] *= 1.0 / math.sqrt(max(b, 1))
+    nrm2 = 1.0 + np.sum(np.where(below, np.abs(a) ** 2, 0.0), axis=0)[:K1]
+    if complex_:
+        theta = uniform(seed, 53, (K1,), 0.0, 2.0 * math.pi)
+        tau = (1.0 - np.exp(1j * theta)) / nrm2
+    else:
+        tau = 2.0 / nrm2
+    return a, np.ascontiguousarray(tau.astype(dt))
+
+
 # ----------------------------------------------------------------------------
 # named workloads
 # ----------------------------------------------------------------------------

@@ -124,3 +124,25 @@ def test_batch_argument_checks_fail_before_any_device_work(L):
     assert L.tbbt_batch_create(None, 1, fake, None) == EINVAL
     assert L.tbbt_batch_execute(None, None) == EINVAL
     assert L.tbbt_batch_destroy(None) == 0
+
+
+def test_band_to_full_argument_checks(L):
+    # rejected (or a no-op) on the host, before any CUDA call
+    buf = (ctypes.c_double * 4)()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    EINVAL = 1
+    for f in (L.tbbt_trans_ev_band_to_full_d, L.tbbt_trans_ev_band_to_full_z):
+        assert f(p, 10, p, 10, 0, 5, p, 10, None) == EINVAL  # nbw < 1
+        assert f(p, 10, p, 10, 4, 11, p, 10, None) == EINVAL  # nev > n
+        assert f(p, 10, p, 10, 4, -1, p, 10, None) == EINVAL  # nev < 0
+        assert f(p, 9, p, 10, 4, 5, p, 10, None) == EINVAL  # lda < n
+        assert f(p, 10, p, 10, 4, 5, p, 9, None) == EINVAL  # ldq < n
+        assert f(p, 10, p, -1, 4, 0, p, 10, None) == EINVAL  # n < 0
+        assert f(None, 10, p, 10, 4, 5, p, 10, None) == EINVAL  # null a
+        assert f(p, 10, None, 10, 4, 5, p, 10, None) == EINVAL  # null tau
+        assert f(p, 10, p, 10, 4, 5, None, 10, None) == EINVAL  # null q
+        assert f(None, 10, None, 10, 10, 5, None, 10, None) == 0  # nbw >= n: identity, nothing to do
+        assert f(None, 10, None, 10, 4, 0, None, 10, None) == 0  # nev = 0
+        assert f(None, 1, None, 0, 4, 0, None, 1, None) == 0  # n = 0
+    odd = ctypes.c_void_p(ctypes.addressof(buf) + 4)
+    assert L.tbbt_trans_ev_band_to_full_d(p, 10, p, 10, 4, 5, odd, 10, None) == EINVAL  # misaligned q
