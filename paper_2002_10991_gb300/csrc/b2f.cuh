@@ -14,8 +14,10 @@
 // recurrence in FP64). Blocks are applied last-first. FP64 on GB300 runs at
 // 2 DFMA per clock per SM, two orders of magnitude below shared-memory and
 // L2 rates, so the kernel is FP64-pipe bound once the pipe is kept fed:
-//   * one thread block per strip of <= 32 columns of Y, grid sized to the
-//     SMs x resident blocks, applies every block to its strip;
+//   * one thread block per strip of <= 16 columns of Y (whole column quads,
+//     one warp each), grid sized to the SMs x resident blocks, applies every
+//     block to its strip; strips of balanced quad counts keep each SM's
+//     FP64 pipe equally loaded;
 //   * one pass over the rows per block boundary: the rows of a 64-row chunk
 //     (32 for complex) get the update of block p+1, Y -= V_{p+1} W_{p+1},
 //     and then feed W_p += V_p^H Y of the next block, so Y is read and
@@ -30,8 +32,7 @@ namespace tbbt {
 namespace bf {
 
 constexpr int NB = 32;        // reflectors per WY block
-constexpr int THREADS = 256;  // threads per block
-constexpr int WMAX = 32;      // columns per strip at most
+constexpr int THREADS = 256;  // threads of the T-factor kernel
 constexpr int PADT = NB + 1;  // padded row length of t-major tiles
 
 template <typename T>
@@ -161,46 +162,61 @@ struct ApplyArgs {
   int32_t nev, grid;
 };
 
+// Apply kernel geometry: 4 warps, warp k owns columns 4k .. 4k+3 of the
+// strip (a column quad), so a strip of w columns keeps ceil(w/4) warps busy
+// and the others skip the arithmetic entirely: every DFMA issued is work.
+// Within a warp, lane = 8 * (column in quad) + row group.
+constexpr int ATHREADS = 128;
+constexpr int AW = 16;  // columns per strip at most (4 quads)
+
 template <typename T, int RC>
 struct Smem {
-  T Zs[WMAX][RC];    // Y chunk, column-major
+  T Zs[AW][RC + 2];  // Y chunk, column-major, padded: the 4 columns of a quad in distinct banks
   T Vu[NB][RC];      // V of the updating block, t-major
   T Va[RC][PADT];    // V of the accumulating block, r-major
-  T Wu[NB][PADT];    // T_u V_u^H Y of the updating block
-  T Wt[NB][PADT];    // V_a^H Y of the accumulating block, before T
+  T Wu[NB][AW + 1];  // T_u V_u^H Y of the updating block
+  T Wt[NB][AW + 1];  // V_a^H Y of the accumulating block, before T
   T Ts[NB][PADT];    // T of the accumulating block
 };
 
 template <typename T, int RC>
-__global__ void __launch_bounds__(THREADS, 2) bf_apply_kernel(ApplyArgs A) {
-  constexpr int NCG = THREADS / RC;   // column groups of the update
-  constexpr int MAXU = WMAX / NCG;    // update columns per thread
-  constexpr int NLD = RC * WMAX / THREADS;  // loaded elements per thread per tile
-  static_assert(RC * NB == RC * WMAX, "V and Y tiles have the same shape");
+__global__ void __launch_bounds__(ATHREADS, 3) bf_apply_kernel(ApplyArgs A) {
+  constexpr int RPT = RC / 8;                   // update rows per thread
+  constexpr int NZ = AW * RC / ATHREADS;        // Y elements loaded per thread per chunk
+  constexpr int NV = NB * RC / ATHREADS;        // V elements loaded per thread per chunk and block
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<T, RC> &S = *reinterpret_cast<Smem<T, RC> *>(smem_raw);
   const Geo &g = A.g;
   const int tid = threadIdx.x;
-  const int32_t j0 = (int32_t)((int64_t)A.nev * blockIdx.x / A.grid);
-  const int32_t w = (int32_t)((int64_t)A.nev * (blockIdx.x + 1) / A.grid) - j0;
+  const int32_t quads = (A.nev + 3) / 4;
+  const int32_t q0 = (int32_t)((int64_t)quads * blockIdx.x / A.grid);
+  const int32_t q1 = (int32_t)((int64_t)quads * (blockIdx.x + 1) / A.grid);
+  const int32_t j0 = 4 * q0;
+  const int32_t w = min(4 * q1, A.nev) - j0;  // 1 .. 16
   T *__restrict__ q = reinterpret_cast<T *>(A.q) + (int64_t)j0 * A.ldq;
   const T *__restrict__ Tws = reinterpret_cast<const T *>(A.Tws);
 
-  const int ur = tid % RC, ucg = tid / RC;  // update: row, column group
-  const int nu = (w - ucg + NCG - 1) / NCG;
-  const int at = tid % NB, acg = tid / NB;  // accumulate: reflector, column group (8 groups)
-  const int na = (w - acg + 7) / 8;
+  const int warp = tid / 32, lane = tid % 32;
+  const bool active = 4 * warp < w;        // warp-uniform
+  const int rg = lane % 8;                 // row group (update) / reflector group (accumulate)
+  const int c = 4 * warp + lane / 8;       // this lane's column
+  const bool live = c < w;                 // false only in a partial last quad
 
-  T zr[NLD], vur[NLD], var[NLD];
+  T zr[NZ], vur[NV], var[NV];
   auto load = [&](int32_t r0, int pu, int pa) {
 #pragma unroll
-    for (int i = 0; i < NLD; ++i) {
-      const int e = tid + THREADS * i;
-      const int r = e % RC, c = e / RC;
+    for (int i = 0; i < NZ; ++i) {
+      const int e = tid + ATHREADS * i;
+      const int r = e % RC, cc = e / RC;
       const int32_t row = r0 + r;
-      zr[i] = (c < w && row < g.n) ? q[(int64_t)c * A.ldq + row] : Ops<T>::zero();
-      vur[i] = pu >= 0 ? vget<T>(g, row, pu, c) : Ops<T>::zero();
-      var[i] = pa >= 0 ? vget<T>(g, row, pa, c) : Ops<T>::zero();
+      zr[i] = (cc < w && row < g.n) ? q[(int64_t)cc * A.ldq + row] : Ops<T>::zero();
+    }
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      const int e = tid + ATHREADS * i;
+      const int r = e % RC, t = e / RC;
+      vur[i] = pu >= 0 ? vget<T>(g, r0 + r, pu, t) : Ops<T>::zero();
+      var[i] = pa >= 0 ? vget<T>(g, r0 + r, pa, t) : Ops<T>::zero();
     }
   };
 
@@ -213,61 +229,66 @@ __global__ void __launch_bounds__(THREADS, 2) bf_apply_kernel(ApplyArgs A) {
     load(rs, pu, pa);
     for (int32_t r0 = rs; r0 < g.n; r0 += RC) {
 #pragma unroll
-      for (int i = 0; i < NLD; ++i) {
-        const int e = tid + THREADS * i;
-        const int r = e % RC, c = e / RC;
-        S.Zs[c][r] = zr[i];
-        S.Vu[c][r] = vur[i];
-        S.Va[r][c] = var[i];
+      for (int i = 0; i < NZ; ++i) {
+        const int e = tid + ATHREADS * i;
+        S.Zs[e / RC][e % RC] = zr[i];
+      }
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        const int e = tid + ATHREADS * i;
+        const int r = e % RC, t = e / RC;
+        S.Vu[t][r] = vur[i];
+        S.Va[r][t] = var[i];
       }
       __syncthreads();
       if (r0 + RC < g.n) load(r0 + RC, pu, pa);
-      if (pu >= 0) {
-        T z[MAXU];
+      if (pu >= 0 && active) {
+        // Y[r][c] -= sum_t V_u[r][t] W_u[t][c], rows r = 8 j + rg
+        T z[RPT];
 #pragma unroll
-        for (int i = 0; i < MAXU; ++i)
-          if (i < nu) z[i] = S.Zs[ucg + NCG * i][ur];
+        for (int j = 0; j < RPT; ++j) z[j] = S.Zs[c][8 * j + rg];
 #pragma unroll 4
         for (int t = 0; t < NB; ++t) {
-          const T vt = S.Vu[t][ur];
+          const T wt = S.Wu[t][c];
 #pragma unroll
-          for (int i = 0; i < MAXU; ++i)
-            if (i < nu) Ops<T>::msub(z[i], vt, S.Wu[t][ucg + NCG * i]);
+          for (int j = 0; j < RPT; ++j) Ops<T>::msub(z[j], S.Vu[t][8 * j + rg], wt);
         }
 #pragma unroll
-        for (int i = 0; i < MAXU; ++i)
-          if (i < nu) {
-            S.Zs[ucg + NCG * i][ur] = z[i];
-            if (r0 + ur < g.n) q[(int64_t)(ucg + NCG * i) * A.ldq + r0 + ur] = z[i];
-          }
+        for (int j = 0; j < RPT; ++j) {
+          S.Zs[c][8 * j + rg] = z[j];
+          const int32_t row = r0 + 8 * j + rg;
+          if (live && row < g.n) q[(int64_t)c * A.ldq + row] = z[j];
+        }
       }
       __syncthreads();
-      if (pa >= 0) {
+      if (pa >= 0 && active) {
+        // W_a[t][c] += sum_r conj(V_a[r][t]) Y[r][c], t = 8 i + rg
 #pragma unroll 4
         for (int r = 0; r < RC; ++r) {
-          const T vr = S.Va[r][at];
+          const T y = S.Zs[c][r];
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
-            if (i < na) Ops<T>::macc(wacc[i], vr, S.Zs[acg + 8 * i][r]);
+          for (int i = 0; i < 4; ++i) Ops<T>::macc(wacc[i], S.Va[r][8 * i + rg], y);
         }
       }
       __syncthreads();
     }
     if (pa >= 0) {
       // W_a <- T_a (V_a^H Y): the next pass's update
+      if (active) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-        if (i < na) S.Wt[at][acg + 8 * i] = wacc[i];
-      for (int e = tid; e < NB * NB; e += THREADS) S.Ts[e % NB][e / NB] = Tws[(int64_t)pa * NB * NB + e];
+        for (int i = 0; i < 4; ++i) S.Wt[8 * i + rg][c] = wacc[i];
+      }
+      for (int e = tid; e < NB * NB; e += ATHREADS) S.Ts[e % NB][e / NB] = Tws[(int64_t)pa * NB * NB + e];
       __syncthreads();
+      if (active) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-        if (i < na) {
-          const int c = acg + 8 * i;
+        for (int i = 0; i < 4; ++i) {
+          const int t = 8 * i + rg;
           T s = Ops<T>::zero();
-          for (int l = at; l < NB; ++l) Ops<T>::mac(s, S.Ts[at][l], S.Wt[l][c]);
-          S.Wu[at][c] = s;
+          for (int l = t; l < NB; ++l) Ops<T>::mac(s, S.Ts[t][l], S.Wt[l][c]);
+          S.Wu[t][c] = s;
         }
+      }
       __syncthreads();
     }
   }

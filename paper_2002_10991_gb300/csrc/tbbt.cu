@@ -1026,15 +1026,16 @@ tbbt_status band_to_full_impl(const T *a, int64_t lda, const T *tau, int64_t n, 
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bf::bf_apply_kernel<T, RC>, bf::THREADS, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bf::bf_apply_kernel<T, RC>, bf::ATHREADS, smem) !=
             cudaSuccess ||
         per_sm < 1) {
       rs = TBBT_ECUDA;
       break;
     }
-    // strips of <= 32 columns, as many as fit at once (balanced widths)
+    // strips of whole column quads, <= 4 quads each, as many as fit at once
+    const int64_t quads = (nev + 3) / 4;
     const int64_t slots = (int64_t)std::max(sms, 1) * per_sm;
-    const int64_t grid = std::max<int64_t>((nev + bf::WMAX - 1) / bf::WMAX, std::min<int64_t>(nev, slots));
+    const int64_t grid = std::max<int64_t>((quads + 3) / 4, std::min<int64_t>(quads, slots));
     bf::ApplyArgs A;
     A.g = g;
     A.Tws = Tws;
@@ -1042,7 +1043,7 @@ tbbt_status band_to_full_impl(const T *a, int64_t lda, const T *tau, int64_t n, 
     A.ldq = ldq;
     A.nev = (int32_t)nev;
     A.grid = (int32_t)grid;
-    bf::bf_apply_kernel<T, RC><<<(unsigned)grid, bf::THREADS, smem, s>>>(A);
+    bf::bf_apply_kernel<T, RC><<<(unsigned)grid, bf::ATHREADS, smem, s>>>(A);
     if (cudaGetLastError() != cudaSuccess) rs = TBBT_ECUDA;
   } while (0);
   cudaFreeAsync(Tws, s);
