@@ -14,10 +14,11 @@
 // recurrence in FP64). Blocks are applied last-first. FP64 on GB300 runs at
 // 2 DFMA per clock per SM, two orders of magnitude below shared-memory and
 // L2 rates, so the kernel is FP64-pipe bound once the pipe is kept fed:
-//   * one thread block per strip of <= 16 columns of Y (whole column quads,
-//     one warp each), grid sized to the SMs x resident blocks, applies every
-//     block to its strip; strips of balanced quad counts keep each SM's
-//     FP64 pipe equally loaded;
+//   * one thread block per strip of <= 16 columns of Y (whole column
+//     quads), grid sized to the SMs x resident blocks, applies every block
+//     to its strip; strips of balanced quad counts keep each SM's FP64 pipe
+//     equally loaded, and the four warps of a block split the rows so that
+//     each sub-partition's pipe gets the same share;
 //   * one pass over the rows per block boundary: the rows of a 64-row chunk
 //     (32 for complex) get the update of block p+1, Y -= V_{p+1} W_{p+1},
 //     and then feed W_p += V_p^H Y of the next block, so Y is read and
@@ -47,6 +48,7 @@ struct Ops<double> {
   static __device__ __forceinline__ void msub(double &s, double x, double y) { s = fma(-x, y, s); }
   static __device__ __forceinline__ double neg_mul(double x, double y) { return -(x * y); }
   static __device__ __forceinline__ double ldro(const double *p) { return __ldg(p); }
+  static __device__ __forceinline__ double add(double x, double y) { return x + y; }
 };
 
 template <>
@@ -74,6 +76,7 @@ struct Ops<zdouble> {
   static __device__ __forceinline__ zdouble neg_mul(zdouble x, zdouble y) {
     return zdouble{-(x.re * y.re - x.im * y.im), -(x.re * y.im + x.im * y.re)};
   }
+  static __device__ __forceinline__ zdouble add(zdouble x, zdouble y) { return zdouble{x.re + y.re, x.im + y.im}; }
   static __device__ __forceinline__ zdouble ldro(const zdouble *p) {
     const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
     return zdouble{v.x, v.y};
@@ -162,10 +165,12 @@ struct ApplyArgs {
   int32_t nev, grid;
 };
 
-// Apply kernel geometry: 4 warps, warp k owns columns 4k .. 4k+3 of the
-// strip (a column quad), so a strip of w columns keeps ceil(w/4) warps busy
-// and the others skip the arithmetic entirely: every DFMA issued is work.
-// Within a warp, lane = 8 * (column in quad) + row group.
+// Apply kernel geometry: 4 warps; a strip is 1 .. 4 column quads. Warp k
+// takes rows 16k .. 16k+15 of every 64-row chunk (8k .. 8k+7 of a 32-row
+// complex chunk) for all of the strip's quads, so the four warps, one per
+// SM sub-partition, carry equal FP64 work whatever the strip width, and no
+// DFMA is issued for a column the strip does not have. Within a warp,
+// lane = 8 * (column in quad) + row (or reflector) group.
 constexpr int ATHREADS = 128;
 constexpr int AW = 16;  // columns per strip at most (4 quads)
 
@@ -175,13 +180,14 @@ struct Smem {
   T Vu[NB][RC];      // V of the updating block, t-major
   T Va[RC][PADT];    // V of the accumulating block, r-major
   T Wu[NB][AW + 1];  // T_u V_u^H Y of the updating block
-  T Wt[NB][AW + 1];  // V_a^H Y of the accumulating block, before T
+  T Wt[NB][AW + 1];  // V_a^H Y of the accumulating block, before T (summed over the warps)
   T Ts[NB][PADT];    // T of the accumulating block
 };
 
 template <typename T, int RC>
-__global__ void __launch_bounds__(ATHREADS, 3) bf_apply_kernel(ApplyArgs A) {
-  constexpr int RPT = RC / 8;                   // update rows per thread
+__global__ void __launch_bounds__(ATHREADS, sizeof(T) == 16 ? 2 : 3) bf_apply_kernel(ApplyArgs A) {
+  constexpr int RW = RC / 4;                    // rows per warp per chunk
+  constexpr int RPT = RW / 8;                   // update rows per lane
   constexpr int NZ = AW * RC / ATHREADS;        // Y elements loaded per thread per chunk
   constexpr int NV = NB * RC / ATHREADS;        // V elements loaded per thread per chunk and block
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -191,16 +197,16 @@ __global__ void __launch_bounds__(ATHREADS, 3) bf_apply_kernel(ApplyArgs A) {
   const int32_t quads = (A.nev + 3) / 4;
   const int32_t q0 = (int32_t)((int64_t)quads * blockIdx.x / A.grid);
   const int32_t q1 = (int32_t)((int64_t)quads * (blockIdx.x + 1) / A.grid);
+  const int nq = q1 - q0;                       // 1 .. 4, uniform in the block
   const int32_t j0 = 4 * q0;
   const int32_t w = min(4 * q1, A.nev) - j0;  // 1 .. 16
   T *__restrict__ q = reinterpret_cast<T *>(A.q) + (int64_t)j0 * A.ldq;
   const T *__restrict__ Tws = reinterpret_cast<const T *>(A.Tws);
 
   const int warp = tid / 32, lane = tid % 32;
-  const bool active = 4 * warp < w;        // warp-uniform
-  const int rg = lane % 8;                 // row group (update) / reflector group (accumulate)
-  const int c = 4 * warp + lane / 8;       // this lane's column
-  const bool live = c < w;                 // false only in a partial last quad
+  const int rg = lane % 8;   // row group (update) / reflector group (accumulate)
+  const int cq = lane / 8;   // column within a quad
+  const int rbase = RW * warp;
 
   T zr[NZ], vur[NV], var[NV];
   auto load = [&](int32_t r0, int pu, int pa) {
@@ -223,9 +229,11 @@ __global__ void __launch_bounds__(ATHREADS, 3) bf_apply_kernel(ApplyArgs A) {
   for (int pa = g.P - 1; pa >= -1; --pa) {
     const int pu = (pa + 1 <= g.P - 1) ? pa + 1 : -1;
     const int32_t rs = NB * (pa >= 0 ? pa : pu) + g.b;
-    T wacc[4];
+    T wacc[4][4];  // [quad][i]: W_a[8 i + rg][4 quad + cq], this warp's rows only
 #pragma unroll
-    for (int i = 0; i < 4; ++i) wacc[i] = Ops<T>::zero();
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) wacc[u][i] = Ops<T>::zero();
     load(rs, pu, pa);
     for (int32_t r0 = rs; r0 < g.n; r0 += RC) {
 #pragma unroll
@@ -242,51 +250,82 @@ __global__ void __launch_bounds__(ATHREADS, 3) bf_apply_kernel(ApplyArgs A) {
       }
       __syncthreads();
       if (r0 + RC < g.n) load(r0 + RC, pu, pa);
-      if (pu >= 0 && active) {
-        // Y[r][c] -= sum_t V_u[r][t] W_u[t][c], rows r = 8 j + rg
-        T z[RPT];
+      if (pu >= 0) {
+        // Y[r][c] -= sum_t V_u[r][t] W_u[t][c], rows r = rbase + 8 j + rg
 #pragma unroll
-        for (int j = 0; j < RPT; ++j) z[j] = S.Zs[c][8 * j + rg];
-#pragma unroll 4
-        for (int t = 0; t < NB; ++t) {
-          const T wt = S.Wu[t][c];
+        for (int u = 0; u < 4; ++u) {
+          if (u < nq) {
+            const int c = 4 * u + cq;
+            T z[RPT];
 #pragma unroll
-          for (int j = 0; j < RPT; ++j) Ops<T>::msub(z[j], S.Vu[t][8 * j + rg], wt);
-        }
+            for (int j = 0; j < RPT; ++j) z[j] = S.Zs[c][rbase + 8 * j + rg];
+#pragma unroll 8
+            for (int t = 0; t < NB; ++t) {
+              const T wt = S.Wu[t][c];
 #pragma unroll
-        for (int j = 0; j < RPT; ++j) {
-          S.Zs[c][8 * j + rg] = z[j];
-          const int32_t row = r0 + 8 * j + rg;
-          if (live && row < g.n) q[(int64_t)c * A.ldq + row] = z[j];
+              for (int j = 0; j < RPT; ++j) Ops<T>::msub(z[j], S.Vu[t][rbase + 8 * j + rg], wt);
+            }
+#pragma unroll
+            for (int j = 0; j < RPT; ++j) {
+              const int r = rbase + 8 * j + rg;
+              S.Zs[c][r] = z[j];
+              if (c < w && r0 + r < g.n) q[(int64_t)c * A.ldq + r0 + r] = z[j];
+            }
+          }
         }
       }
       __syncthreads();
-      if (pa >= 0 && active) {
-        // W_a[t][c] += sum_r conj(V_a[r][t]) Y[r][c], t = 8 i + rg
-#pragma unroll 4
-        for (int r = 0; r < RC; ++r) {
-          const T y = S.Zs[c][r];
+      if (pa >= 0) {
+        // W_a[t][c] += sum_r conj(V_a[r][t]) Y[r][c] over this warp's rows, t = 8 i + rg
+        // (the quad loop is outside the row loop so that a quad the strip
+        // lacks is skipped by a branch, not issued as predicated DFMAs)
 #pragma unroll
-          for (int i = 0; i < 4; ++i) Ops<T>::macc(wacc[i], S.Va[r][8 * i + rg], y);
+        for (int u = 0; u < 4; ++u) {
+          if (u < nq) {
+            const int c = 4 * u + cq;
+#pragma unroll 4
+            for (int r = rbase; r < rbase + RW; ++r) {
+              const T y = S.Zs[c][r];
+#pragma unroll
+              for (int i = 0; i < 4; ++i) Ops<T>::macc(wacc[u][i], S.Va[r][8 * i + rg], y);
+            }
+          }
         }
       }
       __syncthreads();
     }
     if (pa >= 0) {
-      // W_a <- T_a (V_a^H Y): the next pass's update
-      if (active) {
+      // sum the warps' partial V_a^H Y, then W_a <- T_a (V_a^H Y): the next pass's update
+      for (int k = 0; k < 4; ++k) {
+        if (warp == k) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) S.Wt[8 * i + rg][c] = wacc[i];
+          for (int u = 0; u < 4; ++u)
+            if (u < nq) {
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                T &dst = S.Wt[8 * i + rg][4 * u + cq];
+                if (k == 0) {
+                  dst = wacc[u][i];
+                } else {
+                  dst = Ops<T>::add(dst, wacc[u][i]);
+                }
+              }
+            }
+        }
+        __syncthreads();
       }
       for (int e = tid; e < NB * NB; e += ATHREADS) S.Ts[e % NB][e / NB] = Tws[(int64_t)pa * NB * NB + e];
       __syncthreads();
-      if (active) {
+      {
+        const int t = tid % NB, cg = tid / NB;  // columns cg, cg+4, cg+8, cg+12
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int t = 8 * i + rg;
-          T s = Ops<T>::zero();
-          for (int l = t; l < NB; ++l) Ops<T>::mac(s, S.Ts[t][l], S.Wt[l][c]);
-          S.Wu[t][c] = s;
+        for (int m = 0; m < 4; ++m) {
+          const int c = cg + 4 * m;
+          if (c < 4 * nq) {
+            T sacc = Ops<T>::zero();
+            for (int l = t; l < NB; ++l) Ops<T>::mac(sacc, S.Ts[t][l], S.Wt[l][c]);
+            S.Wu[t][c] = sacc;
+          }
         }
       }
       __syncthreads();
