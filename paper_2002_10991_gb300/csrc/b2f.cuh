@@ -162,7 +162,8 @@ struct ApplyArgs {
   const void *Tws;
   void *q;
   int64_t ldq;
-  int32_t nev, grid;
+  int32_t nev;
+  int32_t base, extra;  // block i takes base + (i < extra) column quads
 };
 
 // Apply kernel geometry: 4 warps; a strip is 1 .. 4 column quads. Warp k
@@ -194,10 +195,13 @@ __global__ void __launch_bounds__(ATHREADS, sizeof(T) == 16 ? 2 : 3) bf_apply_ke
   Smem<T, RC> &S = *reinterpret_cast<Smem<T, RC> *>(smem_raw);
   const Geo &g = A.g;
   const int tid = threadIdx.x;
-  const int32_t quads = (A.nev + 3) / 4;
-  const int32_t q0 = (int32_t)((int64_t)quads * blockIdx.x / A.grid);
-  const int32_t q1 = (int32_t)((int64_t)quads * (blockIdx.x + 1) / A.grid);
-  const int nq = q1 - q0;                       // 1 .. 4, uniform in the block
+  // The blocks with one quad more are the first ones, which the block
+  // scheduler spreads over distinct SMs before it places a second block on
+  // any SM.
+  const int32_t bi = (int32_t)blockIdx.x;
+  const int32_t q0 = bi * A.base + min(bi, A.extra);
+  const int nq = A.base + (bi < A.extra ? 1 : 0);  // 1 .. 4, uniform in the block
+  const int32_t q1 = q0 + nq;
   const int32_t j0 = 4 * q0;
   const int32_t w = min(4 * q1, A.nev) - j0;  // 1 .. 16
   T *__restrict__ q = reinterpret_cast<T *>(A.q) + (int64_t)j0 * A.ldq;

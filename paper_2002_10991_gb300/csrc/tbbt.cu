@@ -1032,17 +1032,33 @@ tbbt_status band_to_full_impl(const T *a, int64_t lda, const T *tau, int64_t n, 
       rs = TBBT_ECUDA;
       break;
     }
-    // strips of whole column quads, <= 4 quads each, as many as fit at once
+    // strips of whole column quads (<= 4 each). The FP64 pipe of an SM is
+    // shared by its resident blocks, so the time is set by the SM with the
+    // most quads: choose the blocks per SM (k) that minimise that maximum,
+    // the larger k on a tie (more warps to hide latency).
     const int64_t quads = (nev + 3) / 4;
-    const int64_t slots = (int64_t)std::max(sms, 1) * per_sm;
-    const int64_t grid = std::max<int64_t>((quads + 3) / 4, std::min<int64_t>(quads, slots));
+    const int64_t nsm = std::max(sms, 1);
+    int64_t grid = 0, best_load = 0;
+    for (int k = per_sm; k >= 1; --k) {
+      const int64_t G = std::min<int64_t>(quads, nsm * k);
+      const int64_t base = quads / G, extra = quads % G;
+      if (base + (extra ? 1 : 0) > 4) continue;
+      const int64_t rounds = (G + nsm - 1) / nsm;  // blocks per SM
+      const int64_t load = rounds * base + (extra + nsm - 1) / nsm;
+      if (grid == 0 || load < best_load) {
+        grid = G;
+        best_load = load;
+      }
+    }
+    if (grid == 0) grid = (quads + 3) / 4;  // more than 4 quads per SM slot: several waves of 4-quad strips
     bf::ApplyArgs A;
     A.g = g;
     A.Tws = Tws;
     A.q = q;
     A.ldq = ldq;
     A.nev = (int32_t)nev;
-    A.grid = (int32_t)grid;
+    A.base = (int32_t)(quads / grid);
+    A.extra = (int32_t)(quads % grid);
     bf::bf_apply_kernel<T, RC><<<(unsigned)grid, bf::ATHREADS, smem, s>>>(A);
     if (cudaGetLastError() != cudaSuccess) rs = TBBT_ECUDA;
   } while (0);
