@@ -189,8 +189,9 @@ template <typename T, int RC>
 __global__ void __launch_bounds__(ATHREADS, sizeof(T) == 16 ? 2 : 3) bf_apply_kernel(ApplyArgs A) {
   constexpr int RW = RC / 4;                    // rows per warp per chunk
   constexpr int RPT = RW / 8;                   // update rows per lane
-  constexpr int NZ = AW * RC / ATHREADS;        // Y elements loaded per thread per chunk
-  constexpr int NV = NB * RC / ATHREADS;        // V elements loaded per thread per chunk and block
+  constexpr int NZ = AW * RW / 32;              // Y elements loaded per lane per chunk
+  constexpr int NV = NB * RW / 32;              // V elements loaded per lane per chunk and block
+  constexpr int LPR = 32 / RW;                  // lanes per row index in the loads
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<T, RC> &S = *reinterpret_cast<Smem<T, RC> *>(smem_raw);
   const Geo &g = A.g;
@@ -212,21 +213,24 @@ __global__ void __launch_bounds__(ATHREADS, sizeof(T) == 16 ? 2 : 3) bf_apply_ke
   const int cq = lane / 8;   // column within a quad
   const int rbase = RW * warp;
 
+  // Each warp loads, updates and accumulates only its own rows rbase ..
+  // rbase+RW-1 of a chunk, so a pass over the rows needs no block barrier:
+  // the warps run through the chunks independently and meet once per pass.
+  const int lr = rbase + lane % RW;  // the chunk row this lane loads
+  const int lc = lane / RW;          // first column (or reflector) it loads, then every LPR-th
   T zr[NZ], vur[NV], var[NV];
   auto load = [&](int32_t r0, int pu, int pa) {
+    const int32_t row = r0 + lr;
 #pragma unroll
     for (int i = 0; i < NZ; ++i) {
-      const int e = tid + ATHREADS * i;
-      const int r = e % RC, cc = e / RC;
-      const int32_t row = r0 + r;
+      const int cc = lc + LPR * i;
       zr[i] = (cc < w && row < g.n) ? q[(int64_t)cc * A.ldq + row] : Ops<T>::zero();
     }
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
-      const int e = tid + ATHREADS * i;
-      const int r = e % RC, t = e / RC;
-      vur[i] = pu >= 0 ? vget<T>(g, r0 + r, pu, t) : Ops<T>::zero();
-      var[i] = pa >= 0 ? vget<T>(g, r0 + r, pa, t) : Ops<T>::zero();
+      const int t = lc + LPR * i;
+      vur[i] = pu >= 0 ? vget<T>(g, row, pu, t) : Ops<T>::zero();
+      var[i] = pa >= 0 ? vget<T>(g, row, pa, t) : Ops<T>::zero();
     }
   };
 
@@ -241,18 +245,13 @@ __global__ void __launch_bounds__(ATHREADS, sizeof(T) == 16 ? 2 : 3) bf_apply_ke
     load(rs, pu, pa);
     for (int32_t r0 = rs; r0 < g.n; r0 += RC) {
 #pragma unroll
-      for (int i = 0; i < NZ; ++i) {
-        const int e = tid + ATHREADS * i;
-        S.Zs[e / RC][e % RC] = zr[i];
-      }
+      for (int i = 0; i < NZ; ++i) S.Zs[lc + LPR * i][lr] = zr[i];
 #pragma unroll
       for (int i = 0; i < NV; ++i) {
-        const int e = tid + ATHREADS * i;
-        const int r = e % RC, t = e / RC;
-        S.Vu[t][r] = vur[i];
-        S.Va[r][t] = var[i];
+        S.Vu[lc + LPR * i][lr] = vur[i];
+        S.Va[lr][lc + LPR * i] = var[i];
       }
-      __syncthreads();
+      __syncwarp();
       if (r0 + RC < g.n) load(r0 + RC, pu, pa);
       if (pu >= 0) {
         // Y[r][c] -= sum_t V_u[r][t] W_u[t][c], rows r = rbase + 8 j + rg
@@ -278,7 +277,7 @@ __global__ void __launch_bounds__(ATHREADS, sizeof(T) == 16 ? 2 : 3) bf_apply_ke
           }
         }
       }
-      __syncthreads();
+      __syncwarp();
       if (pa >= 0) {
         // W_a[t][c] += sum_r conj(V_a[r][t]) Y[r][c] over this warp's rows, t = 8 i + rg
         // (the quad loop is outside the row loop so that a quad the strip
@@ -296,7 +295,7 @@ __global__ void __launch_bounds__(ATHREADS, sizeof(T) == 16 ? 2 : 3) bf_apply_ke
           }
         }
       }
-      __syncthreads();
+      __syncwarp();
     }
     if (pa >= 0) {
       // sum the warps' partial V_a^H Y, then W_a <- T_a (V_a^H Y): the next pass's update
