@@ -105,7 +105,9 @@ BULGE_WORKLOADS = {"bulge-real-n4096-b64": (4096, 64, False), "bulge-complex-n40
 # band -> full back-transformation (the step after the path): (n, b, nev, complex, seed)
 B2F_WORKLOADS = {"b2f-real-n8192-b64-nev4096": (8192, 64, 4096, False, I.SEED_BASE + 8),
                  "b2f-complex-n4096-b64-nev2048": (4096, 64, 2048, True, I.SEED_BASE + 10),
-                 "b2f-real-n4096-b64-nev2048": (4096, 64, 2048, False, I.SEED_BASE + 11)}
+                 "b2f-real-n4096-b64-nev2048": (4096, 64, 2048, False, I.SEED_BASE + 11),
+                 # a smaller case of the n=8192 launch configuration (64-row chunks) for profiler captures
+                 "b2f-real-n4096-b64-nev4096": (4096, 64, 4096, False, I.SEED_BASE + 12)}
 
 
 def set_workload(name: str):

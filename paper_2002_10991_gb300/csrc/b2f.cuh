@@ -186,7 +186,7 @@ struct Smem {
 };
 
 template <typename T, int RC>
-__global__ void __launch_bounds__(ATHREADS, sizeof(T) == 16 ? 2 : 3) bf_apply_kernel(ApplyArgs A) {
+__global__ void __launch_bounds__(ATHREADS, sizeof(T) == 16 ? 2 : (RC == 32 ? 4 : 3)) bf_apply_kernel(ApplyArgs A) {
   constexpr int RW = RC / 4;                    // rows per warp per chunk
   constexpr int RPT = RW / 8;                   // update rows per lane
   constexpr int NZ = AW * RW / 32;              // Y elements loaded per lane per chunk

@@ -988,6 +988,54 @@ tbbt_status bulge_chase_impl(const T *band, int64_t ldb, int64_t n, int64_t nbw,
 }
 // Band -> full back-transformation (Eq. 6e): T factors of the 32-reflector
 // blocks, then one pass per block boundary over every column strip.
+namespace bfh {
+namespace bf = tbbt::bf;
+
+// Strips of whole column quads (<= 4 each). The FP64 pipe of an SM is shared
+// by its resident blocks, so the time is set by the SM with the most quads:
+// choose the blocks per SM (k <= per_sm) that minimise that maximum, the
+// larger k on a tie (more warps to hide latency).
+int64_t pick_grid(int64_t quads, int64_t nsm, int per_sm) {
+  int64_t grid = 0, best_load = 0;
+  for (int k = per_sm; k >= 1; --k) {
+    const int64_t G = std::min<int64_t>(quads, nsm * k);
+    const int64_t base = quads / G, extra = quads % G;
+    if (base + (extra ? 1 : 0) > 4) continue;
+    const int64_t rounds = (G + nsm - 1) / nsm;  // blocks per SM
+    const int64_t load = rounds * base + (extra + nsm - 1) / nsm;
+    if (grid == 0 || load < best_load) {
+      grid = G;
+      best_load = load;
+    }
+  }
+  return grid ? grid : (quads + 3) / 4;  // more than 4 quads per SM slot: several waves of 4-quad strips
+}
+
+template <typename T, int RC>
+tbbt_status launch_apply(const bf::Geo &g, const T *Tws, T *q, int64_t ldq, int64_t nev, int sms, cudaStream_t s) {
+  const size_t smem = sizeof(bf::Smem<T, RC>);
+  int per_sm = 0;
+  if (cudaFuncSetAttribute(bf::bf_apply_kernel<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bf::bf_apply_kernel<T, RC>, bf::ATHREADS, smem) !=
+          cudaSuccess ||
+      per_sm < 1)
+    return TBBT_ECUDA;
+  const int64_t quads = (nev + 3) / 4;
+  const int64_t grid = pick_grid(quads, std::max(sms, 1), per_sm);
+  bf::ApplyArgs A;
+  A.g = g;
+  A.Tws = Tws;
+  A.q = q;
+  A.ldq = ldq;
+  A.nev = (int32_t)nev;
+  A.base = (int32_t)(quads / grid);
+  A.extra = (int32_t)(quads % grid);
+  bf::bf_apply_kernel<T, RC><<<(unsigned)grid, bf::ATHREADS, smem, s>>>(A);
+  return cudaGetLastError() == cudaSuccess ? TBBT_OK : TBBT_ECUDA;
+}
+}  // namespace bfh
+
 template <typename T>
 tbbt_status band_to_full_impl(const T *a, int64_t lda, const T *tau, int64_t n, int64_t nbw, int64_t nev, T *q,
                               int64_t ldq, cudaStream_t s) {
@@ -997,7 +1045,6 @@ tbbt_status band_to_full_impl(const T *a, int64_t lda, const T *tau, int64_t n, 
   if (K1 == 0 || nev == 0) return TBBT_OK;
   if (!a || !tau || !q) return TBBT_EINVAL;
   if (((uintptr_t)q | (uintptr_t)a | (uintptr_t)tau) % alignof(T) != 0) return TBBT_EINVAL;
-  constexpr int RC = sizeof(T) == 16 ? 32 : 64;
   namespace bf = tbbt::bf;
   const int32_t P = (int32_t)((K1 + bf::NB - 1) / bf::NB);
   T *Tws = nullptr;
@@ -1017,50 +1064,21 @@ tbbt_status band_to_full_impl(const T *a, int64_t lda, const T *tau, int64_t n, 
       rs = TBBT_ECUDA;
       break;
     }
-    const size_t smem = sizeof(bf::Smem<T, RC>);
-    if (cudaFuncSetAttribute(bf::bf_apply_kernel<T, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess) {
-      rs = TBBT_ECUDA;
-      break;
-    }
-    int dev = 0, sms = 0, per_sm = 0;
+    int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bf::bf_apply_kernel<T, RC>, bf::ATHREADS, smem) !=
-            cudaSuccess ||
-        per_sm < 1) {
-      rs = TBBT_ECUDA;
-      break;
-    }
-    // strips of whole column quads (<= 4 each). The FP64 pipe of an SM is
-    // shared by its resident blocks, so the time is set by the SM with the
-    // most quads: choose the blocks per SM (k) that minimise that maximum,
-    // the larger k on a tie (more warps to hide latency).
+    // Complex data and narrow strips (under two quads per block at three
+    // blocks per SM) take 32-row chunks: more resident blocks, less fixed
+    // work per pass. Wide real strips take 64-row chunks.
     const int64_t quads = (nev + 3) / 4;
-    const int64_t nsm = std::max(sms, 1);
-    int64_t grid = 0, best_load = 0;
-    for (int k = per_sm; k >= 1; --k) {
-      const int64_t G = std::min<int64_t>(quads, nsm * k);
-      const int64_t base = quads / G, extra = quads % G;
-      if (base + (extra ? 1 : 0) > 4) continue;
-      const int64_t rounds = (G + nsm - 1) / nsm;  // blocks per SM
-      const int64_t load = rounds * base + (extra + nsm - 1) / nsm;
-      if (grid == 0 || load < best_load) {
-        grid = G;
-        best_load = load;
-      }
+    if constexpr (sizeof(T) == 16) {
+      rs = bfh::launch_apply<T, 32>(g, Tws, q, ldq, nev, sms, s);
+    } else {
+      if (quads < 6 * (int64_t)std::max(sms, 1))
+        rs = bfh::launch_apply<T, 32>(g, Tws, q, ldq, nev, sms, s);
+      else
+        rs = bfh::launch_apply<T, 64>(g, Tws, q, ldq, nev, sms, s);
     }
-    if (grid == 0) grid = (quads + 3) / 4;  // more than 4 quads per SM slot: several waves of 4-quad strips
-    bf::ApplyArgs A;
-    A.g = g;
-    A.Tws = Tws;
-    A.q = q;
-    A.ldq = ldq;
-    A.nev = (int32_t)nev;
-    A.base = (int32_t)(quads / grid);
-    A.extra = (int32_t)(quads % grid);
-    bf::bf_apply_kernel<T, RC><<<(unsigned)grid, bf::ATHREADS, smem, s>>>(A);
-    if (cudaGetLastError() != cudaSuccess) rs = TBBT_ECUDA;
   } while (0);
   cudaFreeAsync(Tws, s);
   return rs;
