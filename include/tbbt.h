@@ -286,7 +286,7 @@ tbbt_status tbbt_trans_ev_tridi_to_band_noalloc(tbbt_dtype dtype, const void *hh
  * ((2 nbw + 1) x n elements) and small tables are allocated stream-ordered
  * and released by the call. Errors: TBBT_EINVAL (shape, ldb, null pointer
  * with n > 0), TBBT_ENOTSUP (nbw too wide for the shared-memory block:
- * nbw > 118 complex), TBBT_ECUDA; bounded in-kernel waits record
+ * nbw > 117 complex), TBBT_ECUDA; bounded in-kernel waits record
  * TBBT_ETIMEOUT (see tbbt_stream_check).
  * ------------------------------------------------------------------------- */
 tbbt_status tbbt_bulge_chase_d(const double *band, int64_t ldb, int64_t n, int64_t nbw, double *hh_v, double *hh_tau,

@@ -29,6 +29,8 @@
 // Within a sweep the three updates touch disjoint entries, so after the
 // reflector is built the block's warps share them: the left and right
 // updates one column / row per warp, the diagonal block in shared memory.
+// The right-update block of a sweep is the next sweep's generation column
+// and left-update region; it stays in shared memory between the two.
 #pragma once
 #include <stdint.h>
 
@@ -144,18 +146,38 @@ __device__ inline int wait_progress(int *err, long long timeout_ns, const int *f
   }
 }
 
-template <typename T>
+// Barrier among the 128 threads of warps 4..7 (id 2).
+__device__ __forceinline__ void bar_upper() { asm volatile("bar.sync 2, 128;\n" ::: "memory"); }
+
+// Shared memory of the bulge kernel, in elements of T: the reflector, the
+// diagonal block, y = D v with its four partial sums, and (KEEP) the
+// right-update block kept on chip for the next sweep.
+__host__ __device__ constexpr int64_t bc_smem_elems(int b, bool keep) {
+  return (int64_t)kBcMaxB * 6 + (int64_t)b * b * (keep ? 2 : 1);
+}
+
+// KEEP: the right-update block of sweep j (rows r+L .. r+L+b-1, columns
+// r .. r+L-1) stays in shared memory. It is exactly the next sweep's
+// generation column and left-update columns, so sweep j+1 builds its
+// reflector and runs its left update on chip, then writes the block back to
+// L2 (before its progress release; stage i+1 first reads those entries at
+// its sweep j, after progress j+3). Without KEEP (large b) every sweep reads
+// and writes the band at L2.
+template <typename T, bool KEEP>
 __global__ void __launch_bounds__(256, 1) bulge_kernel(BcArgs<T> a) {
   using O = Ops<T>;
+  constexpr int EPL = kBcMaxB / 32;  // elements per lane, at most
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = a.g.b;
   T *sv = reinterpret_cast<T *>(smem_raw);  // reflector, b
   T *sD = sv + kBcMaxB;                     // diagonal block, b x b (column-major, ld b)
-  T *sy = sD + (int64_t)b * b;              // work vector, b
+  T *sy = sD + (int64_t)b * b;              // y = D v, b
+  T *sy4 = sy + kBcMaxB;                    // partial sums of y, 4 x kBcMaxB
+  T *sR = sy4 + 4 * kBcMaxB;                // KEEP: right block, sR[t + s b] = A[r + t, c + s] of the next sweep
   __shared__ T s_tau;
   __shared__ int s_stage;
   __shared__ int s_stop;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int32_t n = a.g.n;
   for (;;) {
     if (tid == 0) {
@@ -183,40 +205,53 @@ __global__ void __launch_bounds__(256, 1) bulge_kernel(BcArgs<T> a) {
       const int64_t r = i + 1 + (int64_t)j * b;
       const int L = (int)((n - r < b) ? n - r : b);
       const int64_t c = (j == 0) ? i : r - b;
+      const bool on_chip = KEEP && j > 0;  // generation and left-update columns are in sR
       // ---- the reflector of column c, rows r .. r+L-1 (one warp)
       if (warp == 0) {
+        T xv[EPL];
         double s2 = 0.0;
-        for (int t = 1 + lane; t < L; t += 32) {
-          const T x = ldw(bat(a, r + t, c));
-          s2 = fma(O::re(x), O::re(x), s2);
-          s2 = fma(O::im(x), O::im(x), s2);
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) {
+          const int t = lane + 32 * e;
+          xv[e] = (t < L) ? (on_chip ? sR[t] : ldw(bat(a, r + t, c))) : O::zero();
+          if (t >= 1) {
+            s2 = fma(O::re(xv[e]), O::re(xv[e]), s2);
+            s2 = fma(O::im(xv[e]), O::im(xv[e]), s2);
+          }
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-        const T alpha = ldw(bat(a, r, c));
+        const double ar = __shfl_sync(0xffffffffu, O::re(xv[0]), 0);
+        const double ai = __shfl_sync(0xffffffffu, O::im(xv[0]), 0);
         T tau, scal;
         double beta;
-        if (s2 == 0.0 && O::im(alpha) == 0.0) {
+        if (s2 == 0.0 && ai == 0.0) {
           tau = O::zero();
-          beta = O::re(alpha);
+          beta = ar;
           scal = O::zero();
         } else {
-          const double nrm = sqrt(O::re(alpha) * O::re(alpha) + O::im(alpha) * O::im(alpha) + s2);
-          beta = O::re(alpha) >= 0.0 ? -nrm : nrm;
+          const double nrm = sqrt(ar * ar + ai * ai + s2);
+          beta = ar >= 0.0 ? -nrm : nrm;
           // tau = (beta - alpha) / beta, scal = 1 / (alpha - beta)
-          tau = O::make((beta - O::re(alpha)) / beta, -O::im(alpha) / beta);
-          const double dr = O::re(alpha) - beta, di = O::im(alpha);
+          tau = O::make((beta - ar) / beta, -ai / beta);
+          const double dr = ar - beta, di = ai;
           const double den = dr * dr + di * di;
           scal = O::make(dr / den, -di / den);
         }
-        for (int t = lane; t < L; t += 32) {
-          T vt;
-          if (t == 0) vt = O::make(1.0, 0.0);
-          else vt = (O::re(scal) == 0.0 && O::im(scal) == 0.0) ? O::zero() : O::mul(ldw(bat(a, r + t, c)), scal);
-          sv[t] = vt;
+        const bool zs = O::re(scal) == 0.0 && O::im(scal) == 0.0;
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) {
+          const int t = lane + 32 * e;
+          if (t < L) {
+            sv[t] = (t == 0) ? O::make(1.0, 0.0) : (zs ? O::zero() : O::mul(xv[e], scal));
+            const T piv = (t == 0) ? O::make(beta, 0.0) : O::zero();
+            if (on_chip)
+              sR[t] = piv;
+            else
+              stw(bat(a, r + t, c), piv);
+          }
         }
         __syncwarp();
-        for (int t = lane; t < L; t += 32) stw(bat(a, r + t, c), (t == 0) ? O::make(beta, 0.0) : O::zero());
         if (lane == 0) s_tau = tau;
         // the canonical store
         const int64_t k = a.stage_off[i] + j;
@@ -229,51 +264,110 @@ __global__ void __launch_bounds__(256, 1) bulge_kernel(BcArgs<T> a) {
       // The left / right updates (warps 4..7) and the diagonal block (warps
       // 0..3) touch disjoint entries and run side by side.
       if (warp >= 4) {
-        // ---- left: rows r .. r+L-1, columns c+1 .. r-1, and right: rows
-        // r+L .. min(r+L+b, n)-1, columns r .. r+L-1. A warp takes CB columns
-        // (rows) at a time: all their loads are issued before the reductions,
-        // and the values stay in registers for the update.
-        constexpr int CB = 4;              // columns (rows) per batch
-        constexpr int EPL = kBcMaxB / 32;  // elements per lane, at most
-        const int64_t ncl = r - (c + 1);   // left columns
+        constexpr int CB = 4;  // columns (rows) per batch
+        const int w4 = warp - 4;
         const int64_t rend = (r + L + b < n) ? r + L + b : n;
         const int64_t nrr = rend - (r + L);  // right rows
-        const int64_t nbl = (ncl + CB - 1) / CB, nbr = (nrr + CB - 1) / CB;
-        for (int64_t bi = warp - 4; bi < nbl + nbr; bi += nw - 4) {
-          const bool left = bi < nbl;
-          const int64_t first = left ? c + 1 + bi * CB : r + L + (bi - nbl) * CB;
-          const int64_t last = left ? r : rend;  // exclusive
+        if (on_chip) {
+          // ---- left, on chip: columns c+1 .. r-1 are sR columns 1 .. b-1
+          for (int s0 = 1 + CB * w4; s0 < b; s0 += CB * 4) {
+            T x[CB][EPL];
+            T wsum[CB];
+#pragma unroll
+            for (int q = 0; q < CB; ++q) {
+              wsum[q] = O::zero();
+#pragma unroll
+              for (int e = 0; e < EPL; ++e) {
+                const int t = lane + 32 * e;
+                x[q][e] = (s0 + q < b && t < L) ? sR[t + (s0 + q) * b] : O::zero();
+                if (t < L) wsum[q] = O::fma_(O::conj(sv[t]), x[q][e], wsum[q]);
+              }
+            }
+#pragma unroll
+            for (int q = 0; q < CB; ++q) {
+              const T f = O::mul(ctau, warp_sum(wsum[q]));
+              if (s0 + q >= b) continue;
+#pragma unroll
+              for (int e = 0; e < EPL; ++e) {
+                const int t = lane + 32 * e;
+                if (t < L) sR[t + (s0 + q) * b] = sub(x[q][e], O::mul(f, sv[t]));
+              }
+            }
+          }
+          bar_upper();
+          // the block is final for this stage: back to L2 (coalesced down each column)
+          for (int idx = tid - 128; idx < L * b; idx += 128) {
+            const int t = idx % L, s = idx / L;
+            stw(bat(a, r + t, c + s), sR[t + s * b]);
+          }
+          bar_upper();  // every read of sR done before the right update refills it
+        } else if (!KEEP) {
+          // ---- left at L2: rows r .. r+L-1, columns c+1 .. r-1
+          const int64_t ncl = r - (c + 1);
+          for (int64_t s0 = c + 1 + CB * w4; s0 < r; s0 += CB * 4) {
+            T x[CB][EPL];
+#pragma unroll
+            for (int q = 0; q < CB; ++q)
+#pragma unroll
+              for (int e = 0; e < EPL; ++e) {
+                const int t = lane + 32 * e;
+                x[q][e] = (s0 + q < r && t < L) ? ldw(bat(a, r + t, s0 + q)) : O::zero();
+              }
+#pragma unroll
+            for (int q = 0; q < CB; ++q) {
+              T wsum = O::zero();
+#pragma unroll
+              for (int e = 0; e < EPL; ++e) {
+                const int t = lane + 32 * e;
+                if (t < L) wsum = O::fma_(O::conj(sv[t]), x[q][e], wsum);
+              }
+              const T f = O::mul(ctau, warp_sum(wsum));
+              if (s0 + q >= r) continue;
+#pragma unroll
+              for (int e = 0; e < EPL; ++e) {
+                const int t = lane + 32 * e;
+                if (t < L) stw(bat(a, r + t, s0 + q), sub(x[q][e], O::mul(f, sv[t])));
+              }
+            }
+          }
+          (void)ncl;
+        }
+        // ---- right: rows r+L .. rend-1, columns r .. r+L-1 (A <- A H); a
+        // warp takes CB rows at a time, loads first, values kept in registers
+        for (int64_t k0 = r + L + CB * w4; k0 < rend; k0 += CB * 4) {
           T x[CB][EPL];
 #pragma unroll
           for (int q = 0; q < CB; ++q)
 #pragma unroll
             for (int e = 0; e < EPL; ++e) {
               const int t = lane + 32 * e;
-              const int64_t k = first + q;
-              x[q][e] = (k < last && t < L) ? ldw(left ? bat(a, r + t, k) : bat(a, k, r + t)) : O::zero();
+              x[q][e] = (k0 + q < rend && t < L) ? ldw(bat(a, k0 + q, r + t)) : O::zero();
             }
 #pragma unroll
           for (int q = 0; q < CB; ++q) {
-            const int64_t k = first + q;
             T wsum = O::zero();
 #pragma unroll
             for (int e = 0; e < EPL; ++e) {
               const int t = lane + 32 * e;
-              if (t < L) wsum = left ? O::fma_(O::conj(sv[t]), x[q][e], wsum) : O::fma_(x[q][e], sv[t], wsum);
+              if (t < L) wsum = O::fma_(x[q][e], sv[t], wsum);
             }
-            wsum = warp_sum(wsum);
-            if (k >= last) continue;
-            const T f = O::mul(left ? ctau : tau, wsum);
+            const T f = O::mul(tau, warp_sum(wsum));
+            const int64_t k = k0 + q;
+            if (k >= rend) continue;
 #pragma unroll
             for (int e = 0; e < EPL; ++e) {
               const int t = lane + 32 * e;
               if (t < L) {
-                if (left) stw(bat(a, r + t, k), sub(x[q][e], O::mul(f, sv[t])));
-                else stw(bat(a, k, r + t), sub(x[q][e], O::mul(f, O::conj(sv[t]))));
+                const T nv = sub(x[q][e], O::mul(f, O::conj(sv[t])));
+                if (KEEP)
+                  sR[(k - (r + L)) + (int64_t)t * b] = nv;  // row k - (r+L) of the next sweep's block, column t
+                else
+                  stw(bat(a, k, r + t), nv);
               }
             }
           }
         }
+        (void)nrr;
       } else {
         // ---- the diagonal block, D <- H^H D H = D - tau y v^H - conj(tau) v y^H
         // + |tau|^2 (v^H y) v v^H with y = D v (D Hermitian: v^H D = y^H)
@@ -283,17 +377,23 @@ __global__ void __launch_bounds__(256, 1) bulge_kernel(BcArgs<T> a) {
           sD[t + s2 * b] = hget(a, r + t, r + s2);
         }
         bar_sub(128);
-        for (int t = bt; t < L; t += 128) {
-          T acc = O::zero();
-          for (int s2 = 0; s2 < L; ++s2) acc = O::fma_(sD[t + s2 * b], sv[s2], acc);
-          sy[t] = acc;
+        // y = D v: warp w sums the quarter w of the columns, then the four add up
+        {
+          const int q0 = (L * warp) / 4, q1 = (L * (warp + 1)) / 4;
+          for (int t = lane; t < L; t += 32) {
+            T acc = O::zero();
+            for (int s2 = q0; s2 < q1; ++s2) acc = O::fma_(sD[t + s2 * b], sv[s2], acc);
+            sy4[warp * kBcMaxB + t] = acc;
+          }
         }
         bar_sub(128);
-        double al = 0.0;  // v^H y (real)
-        for (int t = 0; t < L; ++t) {
-          const T p2 = O::mul(O::conj(sv[t]), sy[t]);
-          al += O::re(p2);
-        }
+        for (int t = bt; t < L; t += 128)
+          sy[t] = add(add(sy4[t], sy4[kBcMaxB + t]), add(sy4[2 * kBcMaxB + t], sy4[3 * kBcMaxB + t]));
+        bar_sub(128);
+        double al = 0.0;  // v^H y (real), every warp reduces it for itself
+        for (int t = lane; t < L; t += 32) al += O::re(O::mul(O::conj(sv[t]), sy[t]));
+#pragma unroll
+        for (int o = 16; o; o >>= 1) al += __shfl_xor_sync(0xffffffffu, al, o);
         const double tt2 = O::re(tau) * O::re(tau) + O::im(tau) * O::im(tau);
         const double cfac = tt2 * al;
         for (int idx = bt; idx < L * L; idx += 128) {
@@ -308,8 +408,10 @@ __global__ void __launch_bounds__(256, 1) bulge_kernel(BcArgs<T> a) {
         }
       }
       __syncthreads();
-      // sweep j of stage i is done: its entries are final for the next stage
-      // (the barrier above orders every thread's stores before this release)
+      // sweep j of stage i is done: what the next stage may read next is in
+      // L2 (the barrier above orders every thread's stores before this
+      // release; with KEEP the block kept on chip is written back during
+      // sweep j+1, before progress j+2)
       if (tid == 0) st_release(mine, j + 1);
     }
     if (abandoned && tid == 0) st_release(mine, kPoison);

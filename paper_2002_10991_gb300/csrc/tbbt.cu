@@ -910,7 +910,10 @@ tbbt_status bulge_chase_impl(const T *band, int64_t ldb, int64_t n, int64_t nbw,
   const StoreGeom g{(int32_t)n, (int32_t)nbw, cplx ? 1 : 0};
   const int64_t K = g.num_reflectors();
   if (K > 0 && (!hh_v || !hh_tau)) return TBBT_EINVAL;
-  const size_t smem = (size_t)(tbbt::bc::kBcMaxB + nbw * nbw + nbw) * sizeof(T);
+  // the right-update block stays on chip when it fits beside the diagonal block
+  const size_t smem_keep = (size_t)tbbt::bc::bc_smem_elems((int)nbw, true) * sizeof(T);
+  const bool keep = smem_keep <= (size_t)kMaxSmem;
+  const size_t smem = keep ? smem_keep : (size_t)tbbt::bc::bc_smem_elems((int)nbw, false) * sizeof(T);
   if (smem > (size_t)kMaxSmem) return TBBT_ENOTSUP;
   const int64_t ldw = 2 * nbw + 1;
   const int32_t nstages = cplx ? (n >= 2 ? (int32_t)n - 1 : 0) : (n >= 3 ? (int32_t)n - 2 : 0);
@@ -949,8 +952,8 @@ tbbt_status bulge_chase_impl(const T *band, int64_t ldb, int64_t n, int64_t nbw,
       break;
     }
     if (nstages > 0) {
-      if (cudaFuncSetAttribute(tbbt::bc::bulge_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-          cudaSuccess) {
+      auto kern = keep ? tbbt::bc::bulge_kernel<T, true> : tbbt::bc::bulge_kernel<T, false>;
+      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         rs = TBBT_ECUDA;
         break;
       }
@@ -972,7 +975,7 @@ tbbt_status bulge_chase_impl(const T *band, int64_t ldb, int64_t n, int64_t nbw,
       a.err = err;
       a.timeout_ns = 20000000000LL;
       const int grid = std::min<int32_t>(nstages, sms > 0 ? sms : 1);
-      tbbt::bc::bulge_kernel<T><<<grid, 256, smem, s>>>(a);
+      kern<<<grid, 256, smem, s>>>(a);
       if (cudaGetLastError() != cudaSuccess) {
         rs = TBBT_ECUDA;
         break;

@@ -54,3 +54,45 @@ def test_lag_three_is_safe_and_two_is_not(n, b, cplx):
             conflicts_lag2 += 1
     if b >= 2 and n >= 4 * b:
         assert conflicts_lag2 > 0  # a lag of two sweeps would race
+
+
+def right_block(n, b, i, j):
+    """The entries the right update of sweep j of stage i writes (empty for j < 0)."""
+    if j < 0:
+        return set()
+    r = i + 1 + j * b
+    L = min(b, n - r)
+    return {(row, r + t) for row in range(r + L, min(r + L + b, n)) for t in range(L)}
+
+
+@pytest.mark.parametrize("n,b,cplx", [(12, 1, False), (20, 2, True), (33, 3, False), (40, 4, True), (57, 5, False),
+                                      (64, 8, False), (50, 7, True)])
+def test_lag_three_is_safe_with_the_right_block_kept_on_chip(n, b, cplx):
+    # The kernel keeps the right-update block of sweep j in shared memory and
+    # writes it back to L2 during sweep j+1 (after that sweep's reflector and
+    # left update have consumed it), before progress j+2 is released. So the
+    # L2 entries that sweep j may hold stale or write are its own entries and
+    # those of the right block of sweep j-1; sweeps that may run at the same
+    # time must still share none.
+    sw = list(sweeps(n, b, cplx))
+    cells = {(i, j): touched(n, b, i, j) | right_block(n, b, i, j - 1) for (i, j) in sw}
+    for (i1, j1), (i0, j0) in itertools.product(sw, sw):
+        if i0 >= i1 or j0 < j1 + 3 * (i1 - i0):
+            continue
+        shared = cells[(i1, j1)] & cells[(i0, j0)]
+        assert not shared, ((i1, j1), (i0, j0), sorted(shared)[:3])
+    # the next sweep's reflector column and left-update columns are exactly
+    # the right block of the sweep before it (what stays on chip)
+    for (i, j) in sw:
+        if j == 0:
+            continue
+        r = i + 1 + j * b
+        L = min(b, n - r)
+        consumed = {(r + t, col) for t in range(L) for col in range(r - b, r)}
+        assert consumed == right_block(n, b, i, j - 1), (i, j)
+    # a stage's last sweep leaves no right block behind (nothing stays on chip)
+    last = {}
+    for (i, j) in sw:
+        last[i] = max(last.get(i, -1), j)
+    for i, j in last.items():
+        assert not right_block(n, b, i, j), (i, j)
