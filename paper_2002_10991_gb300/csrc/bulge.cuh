@@ -161,8 +161,9 @@ __host__ __device__ constexpr int64_t bc_smem_elems(int b, bool keep) {
 // generation column and left-update columns, so sweep j+1 builds its
 // reflector and runs its left update on chip, then writes the block back to
 // L2 (before its progress release; stage i+1 first reads those entries at
-// its sweep j, after progress j+3). Without KEEP (large b) every sweep reads
-// and writes the band at L2.
+// its sweep j, after progress j+3). The last sweep of a stage writes its
+// right block (non-empty when n-i-2 is a multiple of b) straight to L2.
+// Without KEEP (large b) every sweep reads and writes the band at L2.
 template <typename T, bool KEEP>
 __global__ void __launch_bounds__(256, 1) bulge_kernel(BcArgs<T> a) {
   using O = Ops<T>;
@@ -359,10 +360,10 @@ __global__ void __launch_bounds__(256, 1) bulge_kernel(BcArgs<T> a) {
               const int t = lane + 32 * e;
               if (t < L) {
                 const T nv = sub(x[q][e], O::mul(f, O::conj(sv[t])));
-                if (KEEP)
+                if (KEEP && j + 1 < nsweep)
                   sR[(k - (r + L)) + (int64_t)t * b] = nv;  // row k - (r+L) of the next sweep's block, column t
                 else
-                  stw(bat(a, k, r + t), nv);
+                  stw(bat(a, k, r + t), nv);  // no later sweep of this stage consumes it
               }
             }
           }

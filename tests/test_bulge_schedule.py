@@ -90,9 +90,11 @@ def test_lag_three_is_safe_with_the_right_block_kept_on_chip(n, b, cplx):
         L = min(b, n - r)
         consumed = {(r + t, col) for t in range(L) for col in range(r - b, r)}
         assert consumed == right_block(n, b, i, j - 1), (i, j)
-    # a stage's last sweep leaves no right block behind (nothing stays on chip)
+    # a stage's last sweep may leave a right block (when n - i - 2 is a
+    # multiple of b: the fill lands inside the band); no sweep of the stage
+    # consumes it, so the kernel writes that one straight to L2
     last = {}
     for (i, j) in sw:
         last[i] = max(last.get(i, -1), j)
-    for i, j in last.items():
-        assert not right_block(n, b, i, j), (i, j)
+    assert any(right_block(n, b, i, j) for i, j in last.items()) == any(
+        (n - i - 2) % b == 0 and j >= 0 for i, j in last.items() if i <= n - 3)
