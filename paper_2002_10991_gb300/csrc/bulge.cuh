@@ -121,6 +121,12 @@ __device__ __forceinline__ zdouble ldw(const zdouble *p) {
 __device__ __forceinline__ void stw(double *p, double v) { __stcg(p, v); }
 __device__ __forceinline__ void stw(zdouble *p, zdouble v) { __stcg(reinterpret_cast<double2 *>(p), make_double2(v.re, v.im)); }
 
+// Hermitian entry (row, col) from the lower storage.
+template <typename T>
+__device__ __forceinline__ T hget(const BcArgs<T> &a, int64_t row, int64_t col) {
+  return row >= col ? ldw(bat(a, row, col)) : Ops<T>::conj(ldw(bat(a, col, row)));
+}
+
 // Barrier among the first `count` threads of the block (id 1; id 0 is __syncthreads).
 __device__ __forceinline__ void bar_sub(int count) { asm volatile("bar.sync 1, %0;\n" ::"r"(count) : "memory"); }
 
@@ -367,24 +373,9 @@ __global__ void __launch_bounds__(256, 1) bulge_kernel(BcArgs<T> a) {
         // ---- the diagonal block, D <- H^H D H = D - tau y v^H - conj(tau) v y^H
         // + |tau|^2 (v^H y) v v^H with y = D v (D Hermitian: v^H D = y^H)
         const int bt = tid;  // 0 .. 127
-        // the lower triangle from L2, eight loads in flight per thread, mirrored on chip
-        for (int base = 0; base < L * L; base += 128 * 8) {
-          T tmp[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int idx = base + bt + 128 * u;
-            const int t = idx % L, s2 = idx / L;
-            tmp[u] = (idx < L * L && t >= s2) ? ldw(bat(a, r + t, r + s2)) : O::zero();
-          }
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int idx = base + bt + 128 * u;
-            const int t = idx % L, s2 = idx / L;
-            if (idx < L * L && t >= s2) {
-              sD[t + s2 * b] = tmp[u];
-              if (t != s2) sD[s2 + t * b] = O::conj(tmp[u]);
-            }
-          }
+        for (int idx = bt; idx < L * L; idx += 128) {
+          const int t = idx % L, s2 = idx / L;
+          sD[t + s2 * b] = hget(a, r + t, r + s2);
         }
         bar_sub(128);
         // y = D v: warp w sums the quarter w of the columns, then the four add up
