@@ -46,6 +46,7 @@ struct Ops<double> {
   static __device__ __forceinline__ double conj(double x) { return x; }
   static __device__ __forceinline__ double mul(double a, double b) { return a * b; }
   static __device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
+  static __device__ __forceinline__ double fms_(double a, double b, double c) { return fma(-a, b, c); }  // c - a b
   static __device__ __forceinline__ double re(double x) { return x; }
   static __device__ __forceinline__ double im(double) { return 0.0; }
   static __device__ __forceinline__ double make(double r, double) { return r; }
@@ -65,6 +66,15 @@ struct Ops<zdouble> {
     r.re = fma(-a.im, b.im, r.re);
     r.im = fma(a.re, b.im, c.im);
     r.im = fma(a.im, b.re, r.im);
+    return r;
+  }
+  // c - a * b
+  static __device__ __forceinline__ zdouble fms_(zdouble a, zdouble b, zdouble c) {
+    zdouble r;
+    r.re = fma(-a.re, b.re, c.re);
+    r.re = fma(a.im, b.im, r.re);
+    r.im = fma(-a.re, b.im, c.im);
+    r.im = fma(-a.im, b.re, r.im);
     return r;
   }
   static __device__ __forceinline__ double re(zdouble x) { return x.re; }
@@ -153,7 +163,7 @@ __device__ __forceinline__ void bar_upper() { asm volatile("bar.sync 2, 128;\n" 
 // diagonal block, y = D v with its four partial sums, and (KEEP) the
 // right-update block kept on chip for the next sweep.
 __host__ __device__ constexpr int64_t bc_smem_elems(int b, bool keep) {
-  return (int64_t)kBcMaxB * 6 + (int64_t)b * b * (keep ? 2 : 1);
+  return (int64_t)kBcMaxB * 6 + (int64_t)b * b + (keep ? (int64_t)b * (b + 1) : 0);
 }
 
 // KEEP: the right-update block of sweep j (rows r+L .. r+L+b-1, columns
@@ -174,7 +184,8 @@ __global__ void __launch_bounds__(256, 1) bulge_kernel(BcArgs<T> a) {
   T *sD = sv + kBcMaxB;                     // diagonal block, b x b (column-major, ld b)
   T *sy = sD + (int64_t)b * b;              // y = D v, b
   T *sy4 = sy + kBcMaxB;                    // partial sums of y, 4 x kBcMaxB
-  T *sR = sy4 + 4 * kBcMaxB;                // KEEP: right block, sR[t + s b] = A[r + t, c + s] of the next sweep
+  T *sR = sy4 + 4 * kBcMaxB;                // KEEP: right block, sR[t + s ldr] = A[r + t, c + s] of the next sweep
+  const int ldr = b + 1;                    // padded: a thread per row or per column reads without bank conflicts
   __shared__ T s_tau;
   __shared__ int s_stage;
   __shared__ int s_stop;
@@ -214,7 +225,7 @@ __global__ void __launch_bounds__(256, 1) bulge_kernel(BcArgs<T> a) {
 #pragma unroll
         for (int e = 0; e < EPL; ++e) {
           const int t = lane + 32 * e;
-          xv[e] = (t < L) ? (on_chip ? sR[t] : ldw(bat(a, r + t, c))) : O::zero();
+          xv[e] = (t < L) ? (on_chip ? sR[t] : ldw(bat(a, r + t, c))) : O::zero();  // column 0 of sR
           if (t >= 1) {
             s2 = fma(O::re(xv[e]), O::re(xv[e]), s2);
             s2 = fma(O::im(xv[e]), O::im(xv[e]), s2);
@@ -265,46 +276,66 @@ __global__ void __launch_bounds__(256, 1) bulge_kernel(BcArgs<T> a) {
       // The left / right updates (warps 4..7) and the diagonal block (warps
       // 0..3) touch disjoint entries and run side by side.
       if (warp >= 4) {
-        constexpr int CB = 4;  // columns (rows) per batch
-        const int w4 = warp - 4;
+        const int ut = tid - 128;  // 0 .. 127
         const int64_t rend = (r + L + b < n) ? r + L + b : n;
-        const int64_t nrr = rend - (r + L);  // right rows
-        if (on_chip) {
-          // ---- left, on chip: columns c+1 .. r-1 are sR columns 1 .. b-1
-          for (int s0 = 1 + CB * w4; s0 < b; s0 += CB * 4) {
-            T x[CB][EPL];
-            T wsum[CB];
+        const int nrr = (int)(rend - (r + L));  // right rows
+        if constexpr (KEEP) {
+          // One thread per column (left) or row (right) of a padded on-chip
+          // block: dot products and updates are plain FMA chains, no shuffles.
+          if (on_chip) {
+            // ---- left, on chip: columns c+1 .. r-1 are sR columns 1 .. b-1
+            if (ut < b - 1) {
+              T *col = sR + (int64_t)(ut + 1) * ldr;
+              T wsum = O::zero();
+              for (int t = 0; t < L; ++t) wsum = O::fma_(O::conj(sv[t]), col[t], wsum);
+              const T f = O::mul(ctau, wsum);
+              for (int t = 0; t < L; ++t) col[t] = O::fms_(f, sv[t], col[t]);
+            }
+            bar_upper();
+            // the block is final for this stage: back to L2 (coalesced down each column)
+            for (int idx = ut; idx < L * b; idx += 128) {
+              const int t = idx % L, s = idx / L;
+              stw(bat(a, r + t, c + s), sR[t + s * ldr]);
+            }
+            bar_upper();  // every read of sR done before the right update refills it
+          }
+          if (nrr > 0) {
+            // ---- right: rows r+L .. rend-1, columns r .. r+L-1 (A <- A H); the old
+            // values land in sR (row k - (r+L), column t), eight loads in flight per thread
+            const int tot = nrr * L;
+            for (int base = 0; base < tot; base += 128 * 8) {
+              T tmp[8];
 #pragma unroll
-            for (int q = 0; q < CB; ++q) {
-              wsum[q] = O::zero();
+              for (int u = 0; u < 8; ++u) {
+                const int idx = base + ut + 128 * u;
+                tmp[u] = idx < tot ? ldw(bat(a, r + L + idx % nrr, r + idx / nrr)) : O::zero();
+              }
 #pragma unroll
-              for (int e = 0; e < EPL; ++e) {
-                const int t = lane + 32 * e;
-                x[q][e] = (s0 + q < b && t < L) ? sR[t + (s0 + q) * b] : O::zero();
-                if (t < L) wsum[q] = O::fma_(O::conj(sv[t]), x[q][e], wsum[q]);
+              for (int u = 0; u < 8; ++u) {
+                const int idx = base + ut + 128 * u;
+                if (idx < tot) sR[idx % nrr + (idx / nrr) * ldr] = tmp[u];
               }
             }
-#pragma unroll
-            for (int q = 0; q < CB; ++q) {
-              const T f = O::mul(ctau, warp_sum(wsum[q]));
-              if (s0 + q >= b) continue;
-#pragma unroll
-              for (int e = 0; e < EPL; ++e) {
-                const int t = lane + 32 * e;
-                if (t < L) sR[t + (s0 + q) * b] = sub(x[q][e], O::mul(f, sv[t]));
-              }
+            bar_upper();
+            if (ut < nrr) {
+              T wsum = O::zero();
+              for (int t = 0; t < L; ++t) wsum = O::fma_(sR[ut + t * ldr], sv[t], wsum);
+              const T f = O::mul(tau, wsum);
+              for (int t = 0; t < L; ++t) sR[ut + t * ldr] = O::fms_(f, O::conj(sv[t]), sR[ut + t * ldr]);
+            }
+            if (j + 1 == nsweep) {
+              // no later sweep of this stage consumes it: straight to L2
+              bar_upper();
+              for (int idx = ut; idx < tot; idx += 128)
+                stw(bat(a, r + L + idx % nrr, r + idx / nrr), sR[idx % nrr + (idx / nrr) * ldr]);
             }
           }
-          bar_upper();
-          // the block is final for this stage: back to L2 (coalesced down each column)
-          for (int idx = tid - 128; idx < L * b; idx += 128) {
-            const int t = idx % L, s = idx / L;
-            stw(bat(a, r + t, c + s), sR[t + s * b]);
-          }
-          bar_upper();  // every read of sR done before the right update refills it
-        } else if (!KEEP) {
-          // ---- left at L2: rows r .. r+L-1, columns c+1 .. r-1
-          const int64_t ncl = r - (c + 1);
+        } else {
+          // Wide bands: both updates at L2, a warp per batch of CB columns
+          // (rows), loads issued together, values kept in registers.
+          constexpr int CB = 4;
+          const int w4 = warp - 4;
+          // ---- left: rows r .. r+L-1, columns c+1 .. r-1
           for (int64_t s0 = c + 1 + CB * w4; s0 < r; s0 += CB * 4) {
             T x[CB][EPL];
 #pragma unroll
@@ -327,48 +358,39 @@ __global__ void __launch_bounds__(256, 1) bulge_kernel(BcArgs<T> a) {
 #pragma unroll
               for (int e = 0; e < EPL; ++e) {
                 const int t = lane + 32 * e;
-                if (t < L) stw(bat(a, r + t, s0 + q), sub(x[q][e], O::mul(f, sv[t])));
+                if (t < L) stw(bat(a, r + t, s0 + q), O::fms_(f, sv[t], x[q][e]));
               }
             }
           }
-          (void)ncl;
-        }
-        // ---- right: rows r+L .. rend-1, columns r .. r+L-1 (A <- A H); a
-        // warp takes CB rows at a time, loads first, values kept in registers
-        for (int64_t k0 = r + L + CB * w4; k0 < rend; k0 += CB * 4) {
-          T x[CB][EPL];
+          // ---- right: rows r+L .. rend-1, columns r .. r+L-1 (A <- A H)
+          for (int64_t k0 = r + L + CB * w4; k0 < rend; k0 += CB * 4) {
+            T x[CB][EPL];
 #pragma unroll
-          for (int q = 0; q < CB; ++q)
+            for (int q = 0; q < CB; ++q)
 #pragma unroll
-            for (int e = 0; e < EPL; ++e) {
-              const int t = lane + 32 * e;
-              x[q][e] = (k0 + q < rend && t < L) ? ldw(bat(a, k0 + q, r + t)) : O::zero();
-            }
+              for (int e = 0; e < EPL; ++e) {
+                const int t = lane + 32 * e;
+                x[q][e] = (k0 + q < rend && t < L) ? ldw(bat(a, k0 + q, r + t)) : O::zero();
+              }
 #pragma unroll
-          for (int q = 0; q < CB; ++q) {
-            T wsum = O::zero();
+            for (int q = 0; q < CB; ++q) {
+              T wsum = O::zero();
 #pragma unroll
-            for (int e = 0; e < EPL; ++e) {
-              const int t = lane + 32 * e;
-              if (t < L) wsum = O::fma_(x[q][e], sv[t], wsum);
-            }
-            const T f = O::mul(tau, warp_sum(wsum));
-            const int64_t k = k0 + q;
-            if (k >= rend) continue;
+              for (int e = 0; e < EPL; ++e) {
+                const int t = lane + 32 * e;
+                if (t < L) wsum = O::fma_(x[q][e], sv[t], wsum);
+              }
+              const T f = O::mul(tau, warp_sum(wsum));
+              const int64_t k = k0 + q;
+              if (k >= rend) continue;
 #pragma unroll
-            for (int e = 0; e < EPL; ++e) {
-              const int t = lane + 32 * e;
-              if (t < L) {
-                const T nv = sub(x[q][e], O::mul(f, O::conj(sv[t])));
-                if (KEEP && j + 1 < nsweep)
-                  sR[(k - (r + L)) + (int64_t)t * b] = nv;  // row k - (r+L) of the next sweep's block, column t
-                else
-                  stw(bat(a, k, r + t), nv);  // no later sweep of this stage consumes it
+              for (int e = 0; e < EPL; ++e) {
+                const int t = lane + 32 * e;
+                if (t < L) stw(bat(a, k, r + t), O::fms_(f, O::conj(sv[t]), x[q][e]));
               }
             }
           }
         }
-        (void)nrr;
       } else {
         // ---- the diagonal block, D <- H^H D H = D - tau y v^H - conj(tau) v y^H
         // + |tau|^2 (v^H y) v v^H with y = D v (D Hermitian: v^H D = y^H)
@@ -396,14 +418,17 @@ __global__ void __launch_bounds__(256, 1) bulge_kernel(BcArgs<T> a) {
 #pragma unroll
         for (int o = 16; o; o >>= 1) al += __shfl_xor_sync(0xffffffffu, al, o);
         const double tt2 = O::re(tau) * O::re(tau) + O::im(tau) * O::im(tau);
-        const double cfac = tt2 * al;
+        const double half = 0.5 * tt2 * al;
+        // H^H D H = D - w v^H - v w^H with w = tau y - (|tau|^2 (v^H y) / 2) v
+        T *sw = sy4;  // the partial sums are consumed
+        for (int t = bt; t < L; t += 128) sw[t] = O::fms_(O::make(half, 0.0), sv[t], O::mul(tau, sy[t]));
+        bar_sub(128);
         for (int idx = bt; idx < L * L; idx += 128) {
           const int t = idx % L, s2 = idx / L;
           if (t < s2) continue;
           T dv = sD[t + s2 * b];
-          dv = sub(dv, O::mul(O::mul(tau, sy[t]), O::conj(sv[s2])));
-          dv = sub(dv, O::mul(O::mul(ctau, sv[t]), O::conj(sy[s2])));
-          dv = add(dv, O::mul(O::make(cfac, 0.0), O::mul(sv[t], O::conj(sv[s2]))));
+          dv = O::fms_(sw[t], O::conj(sv[s2]), dv);
+          dv = O::fms_(sv[t], O::conj(sw[s2]), dv);
           if (t == s2) dv = O::make(O::re(dv), 0.0);
           stw(bat(a, r + t, r + s2), dv);
         }
