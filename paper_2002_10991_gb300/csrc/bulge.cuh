@@ -163,7 +163,7 @@ __device__ __forceinline__ void bar_upper() { asm volatile("bar.sync 2, 128;\n" 
 // diagonal block, y = D v with its four partial sums, and (KEEP) the
 // right-update block kept on chip for the next sweep.
 __host__ __device__ constexpr int64_t bc_smem_elems(int b, bool keep) {
-  return (int64_t)kBcMaxB * 6 + (int64_t)b * b + (keep ? (int64_t)b * (b + 1) : 0);
+  return (int64_t)kBcMaxB * 6 + (int64_t)b * b + (keep ? (int64_t)b * (b + 1) + 2 * kBcMaxB : 0);
 }
 
 // KEEP: the right-update block of sweep j (rows r+L .. r+L+b-1, columns
@@ -186,6 +186,7 @@ __global__ void __launch_bounds__(256, 1) bulge_kernel(BcArgs<T> a) {
   T *sy4 = sy + kBcMaxB;                    // partial sums of y, 4 x kBcMaxB
   T *sR = sy4 + 4 * kBcMaxB;                // KEEP: right block, sR[t + s ldr] = A[r + t, c + s] of the next sweep
   const int ldr = b + 1;                    // padded: a thread per row or per column reads without bank conflicts
+  T *sPart = sR + (int64_t)b * ldr;         // KEEP: the two half dot products of each column / row
   __shared__ T s_tau;
   __shared__ int s_stage;
   __shared__ int s_stop;
@@ -280,22 +281,31 @@ __global__ void __launch_bounds__(256, 1) bulge_kernel(BcArgs<T> a) {
         const int64_t rend = (r + L + b < n) ? r + L + b : n;
         const int nrr = (int)(rend - (r + L));  // right rows
         if constexpr (KEEP) {
-          // One thread per column (left) or row (right) of a padded on-chip
-          // block: dot products and updates are plain FMA chains, no shuffles.
+          // Two threads per column (left) or row (right) of a padded on-chip
+          // block, each taking half of the rows t: plain FMA chains, no
+          // shuffle reductions, and all four warps (every sub-partition's
+          // FP64 unit) carry an equal share.
+          const int q = ut % 64, h = ut / 64;
+          const int tlo = (L * h) / 2, thi = (L * (h + 1)) / 2;
           if (on_chip) {
             // ---- left, on chip: columns c+1 .. r-1 are sR columns 1 .. b-1
-            if (ut < b - 1) {
-              T *col = sR + (int64_t)(ut + 1) * ldr;
+            for (int sc = 1 + q; sc < b; sc += 64) {
+              const T *col = sR + (int64_t)sc * ldr;
               T wsum = O::zero();
-              for (int t = 0; t < L; ++t) wsum = O::fma_(O::conj(sv[t]), col[t], wsum);
-              const T f = O::mul(ctau, wsum);
-              for (int t = 0; t < L; ++t) col[t] = O::fms_(f, sv[t], col[t]);
+              for (int t = tlo; t < thi; ++t) wsum = O::fma_(O::conj(sv[t]), col[t], wsum);
+              sPart[h * kBcMaxB + sc] = wsum;
+            }
+            bar_upper();
+            for (int sc = 1 + q; sc < b; sc += 64) {
+              T *col = sR + (int64_t)sc * ldr;
+              const T f = O::mul(ctau, add(sPart[sc], sPart[kBcMaxB + sc]));
+              for (int t = tlo; t < thi; ++t) col[t] = O::fms_(f, sv[t], col[t]);
             }
             bar_upper();
             // the block is final for this stage: back to L2 (coalesced down each column)
             for (int idx = ut; idx < L * b; idx += 128) {
-              const int t = idx % L, s = idx / L;
-              stw(bat(a, r + t, c + s), sR[t + s * ldr]);
+              const int t = idx % L, sc = idx / L;
+              stw(bat(a, r + t, c + sc), sR[t + sc * ldr]);
             }
             bar_upper();  // every read of sR done before the right update refills it
           }
@@ -317,11 +327,15 @@ __global__ void __launch_bounds__(256, 1) bulge_kernel(BcArgs<T> a) {
               }
             }
             bar_upper();
-            if (ut < nrr) {
+            for (int kk = q; kk < nrr; kk += 64) {
               T wsum = O::zero();
-              for (int t = 0; t < L; ++t) wsum = O::fma_(sR[ut + t * ldr], sv[t], wsum);
-              const T f = O::mul(tau, wsum);
-              for (int t = 0; t < L; ++t) sR[ut + t * ldr] = O::fms_(f, O::conj(sv[t]), sR[ut + t * ldr]);
+              for (int t = tlo; t < thi; ++t) wsum = O::fma_(sR[kk + t * ldr], sv[t], wsum);
+              sPart[h * kBcMaxB + kk] = wsum;
+            }
+            bar_upper();
+            for (int kk = q; kk < nrr; kk += 64) {
+              const T f = O::mul(tau, add(sPart[kk], sPart[kBcMaxB + kk]));
+              for (int t = tlo; t < thi; ++t) sR[kk + t * ldr] = O::fms_(f, O::conj(sv[t]), sR[kk + t * ldr]);
             }
             if (j + 1 == nsweep) {
               // no later sweep of this stage consumes it: straight to L2
