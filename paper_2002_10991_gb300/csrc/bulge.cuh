@@ -27,10 +27,15 @@
 // release; the waits are bounded (TBBT_ETIMEOUT, then the block gives up).
 //
 // Within a sweep the three updates touch disjoint entries, so after the
-// reflector is built the block's warps share them: the left and right
-// updates one column / row per warp, the diagonal block in shared memory.
-// The right-update block of a sweep is the next sweep's generation column
-// and left-update region; it stays in shared memory between the two.
+// reflector is built the block's warps share them: warps 4..7 the left and
+// right updates, warps 0..3 the diagonal block in shared memory. The
+// right-update block of a sweep is the next sweep's generation column and
+// left-update region; it stays in shared memory between the two. On GB300 a
+// warp-level DFMA holds its sub-partition's FP64 unit for many cycles
+// whatever the number of active lanes, so the updates are written to issue
+// few warp-level FP64 instructions, spread over all four sub-partitions:
+// FMA chains per column / row instead of shuffle reductions, and the
+// diagonal block as the Hermitian rank-2 update D - w v^H - v w^H.
 #pragma once
 #include <stdint.h>
 
@@ -161,7 +166,8 @@ __device__ __forceinline__ void bar_upper() { asm volatile("bar.sync 2, 128;\n" 
 
 // Shared memory of the bulge kernel, in elements of T: the reflector, the
 // diagonal block, y = D v with its four partial sums, and (KEEP) the
-// right-update block kept on chip for the next sweep.
+// right-update block kept on chip for the next sweep (padded to b+1 rows)
+// with the half dot products of its columns / rows.
 __host__ __device__ constexpr int64_t bc_smem_elems(int b, bool keep) {
   return (int64_t)kBcMaxB * 6 + (int64_t)b * b + (keep ? (int64_t)b * (b + 1) + 2 * kBcMaxB : 0);
 }
