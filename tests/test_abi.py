@@ -146,3 +146,14 @@ def test_band_to_full_argument_checks(L):
         assert f(None, 1, None, 0, 4, 0, None, 1, None) == 0  # n = 0
     odd = ctypes.c_void_p(ctypes.addressof(buf) + 4)
     assert L.tbbt_trans_ev_band_to_full_d(p, 10, p, 10, 4, 5, odd, 10, None) == EINVAL  # misaligned q
+
+
+def test_bulge_chase_shape_limits_on_the_host(L):
+    # rejected before any CUDA call: the shared-memory form holds the b x b
+    # diagonal block, which caps a Hermitian band at nbw = 117
+    buf = (ctypes.c_double * 8)()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    ENOTSUP, EINVAL = 5, 1
+    assert L.tbbt_bulge_chase_z(p, 119, 200, 118, p, p, p, p, None) == ENOTSUP
+    assert L.tbbt_bulge_chase_d(p, 129, 200, 129, p, p, p, p, None) == EINVAL  # nbw > 128
+    assert L.tbbt_bulge_chase_d(p, 4, 0, 3, None, None, None, None, None) == 0  # n = 0: nothing to do
