@@ -165,3 +165,23 @@ def test_planted_mistake_is_caught(name, tmp_path):
     with oracle.use_library(path):
         caught = (not _pins_pass(False)) or (not _pins_pass(True))
     assert caught, f"mutation {name} was not caught by the pins"
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_synthetic_full_store_is_unitary_and_fills_unread_entries(cplx):
+    # the GPU parity tests and the benchmark use this store: its reflectors
+    # are unitary (so Q1 keeps column norms), and the entries at or above the
+    # b-th sub-diagonal hold N(0, 1) values, which a kernel that read them
+    # would turn into a parity failure
+    n, b = 90, 7
+    a, tau = I.synthetic_full_store(n, b, 31, cplx)
+    assert a.shape == (n, n) and a.flags.f_contiguous and tau.size == n - b
+    Q = q1_of(a, tau, n, b)
+    assert np.abs(Q.conj().T @ Q - np.eye(n)).max() <= 1e-13 * n
+    i, j = np.indices((n, n))
+    unread = i <= j + b
+    assert np.all(a[unread] != 0)
+    assert np.abs(a[unread]).mean() > 0.5  # N(0, 1) scale, not the N(0, 1/b) tails
+    # the same seed gives the same store
+    a2, tau2 = I.synthetic_full_store(n, b, 31, cplx)
+    assert np.array_equal(a, a2) and np.array_equal(tau, tau2)
