@@ -82,3 +82,19 @@ def test_bulge_chase_rejects_bad_arguments(P):
     assert L.tbbt_bulge_chase_d(p, 4, 10, 0, p, p, p, p, None) == 1  # nbw < 1
     assert L.tbbt_bulge_chase_d(None, 4, 10, 3, p, p, p, p, None) == 1
     assert L.tbbt_bulge_chase_d(None, 4, 0, 3, None, None, None, None, None) == 0
+
+
+def test_bulge_chase_full_size_spectrum(P):
+    # the benchmark's band (n = 8192, b = 64, DFT-like): on such bands the
+    # signs of e, tau and v follow the rounding of near-zero bulge entries, so
+    # the check is what two correct reductions share, the spectrum of T
+    sl = pytest.importorskip("scipy.linalg")
+    n, b = 8192, 64
+    W = I.band_dft(n, b, 2002109910 + n, False)
+    _, _, d, e = P.bulge_chase(to_dev_band(W))
+    P.stream_check()
+    _, _, do, eo = oracle.bulge_chase(W)
+    lam = sl.eigvalsh_tridiagonal(d.cpu().numpy(), e.cpu().numpy())
+    lam_o = sl.eigvalsh_tridiagonal(do, eo)
+    assert np.abs(lam - lam_o).max() <= 1e-10
+    assert np.abs(np.abs(e.cpu().numpy()).sum() - np.abs(eo).sum()) <= 1e-6 * np.abs(eo).sum()
