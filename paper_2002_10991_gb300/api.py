@@ -55,6 +55,27 @@ def schedule_max_live_rows(n: int, nbw: int, is_complex: bool, sweeps_per_block:
     return int(_native.load().tbbt_schedule_max_live_rows(n, nbw, int(is_complex), sweeps_per_block, stages_per_step))
 
 
+def _need_device(t, name: str, dtype=None, min_numel: int = 0):
+    """A device API gets raw pointers: reject what would make a kernel read
+    outside the caller's memory (a host tensor, a mismatched element type, too
+    few elements) before anything reaches the library."""
+    if min_numel <= 0 and t.numel() == 0:
+        return
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} has dtype {t.dtype}, expected {dtype}")
+    if t.numel() < min_numel:
+        raise ValueError(f"{name} has {t.numel()} elements, needs at least {min_numel}")
+
+
+def _need_flat(t, name: str, dtype, numel: int):
+    """A flat (contiguous) device array of at least ``numel`` elements."""
+    _need_device(t, name, dtype, numel)
+    if numel > 0 and not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
 def _q_layout(q, n):
     """(ldq, nev) of a column-major (Fortran-ordered) 2-D tensor view."""
     if q.dim() != 2:
@@ -68,12 +89,33 @@ def _q_layout(q, n):
     return ldq, nev
 
 
+def _check_q(q, n: int, nev: int, dtype):
+    if n > 0 and nev > 0:
+        _need_device(q, "q", dtype, 1)
+        if q.dim() != 2 or q.shape[0] < n or q.shape[1] < nev:
+            raise ValueError(f"q must be at least {n} x {nev}")
+
+
+def _check_store_and_q(hh_v, hh_tau, n: int, nbw: int, nev: int, q, cplx: bool):
+    import torch
+
+    dt = torch.complex128 if cplx else torch.float64
+    if n < 0 or nbw < 1:
+        return  # the library reports the shape error
+    K = num_reflectors(n, nbw, cplx)
+    if K > 0 and nev > 0:
+        _need_flat(hh_v, "hh_v", dt, K * nbw)
+        _need_flat(hh_tau, "hh_tau", dt, K)
+    _check_q(q, n, nev, dt)
+
+
 def trans_ev_tridi_to_band(hh_v, hh_tau, n: int, nbw: int, nev: int, q, ldq: int | None = None, stream=None):
     """Eq. 6d on device tensors: q[:n, :nev] <- H_0 ... H_{K-1} q[:n, :nev].
 
     hh_v (K*nbw,), hh_tau (K,), q (ldq x >=nev, column-major) are CUDA
     tensors of dtype float64 (real symmetric) or complex128 (Hermitian)."""
     cplx = _is_complex_dtype(q)
+    _check_store_and_q(hh_v, hh_tau, n, nbw, nev, q, cplx)
     if ldq is None:
         ldq, _ = _q_layout(q, n)
     L = _native.load()
@@ -94,9 +136,14 @@ def bulge_chase(band, nbw: int | None = None, stream=None):
     import torch
 
     cplx = _is_complex_dtype(band)
+    if band.dim() != 2:
+        raise ValueError("band must be 2-D, (nbw+1) x n")
     if nbw is None:
         nbw = band.shape[0] - 1
     n = band.shape[1]
+    if band.shape[0] < nbw + 1:
+        raise ValueError("band must have at least nbw+1 rows")
+    _need_device(band, "band")
     if band.numel() and band.stride(0) != 1:
         raise ValueError("band must be column-major (stride 1 along the band index)")
     ldb = band.stride(1) if n > 1 else nbw + 1
@@ -125,8 +172,15 @@ def trans_ev_band_to_full(a, tau, n: int, nbw: int, nev: int, q, stream=None):
     v[1:] in a[c+nbw+1:, c]) and ``tau`` (n-nbw entries). float64 or
     complex128 CUDA tensors; q column-major."""
     cplx = _is_complex_dtype(q)
-    if a.dim() != 2 or a.shape[0] < n or (a.shape[1] > 1 and a.stride(0) != 1):
-        raise ValueError("a must be a column-major 2-D tensor with at least n rows")
+    K1 = max(n - nbw, 0) if nbw >= 1 else 0
+    if K1 > 0 and nev > 0:
+        if a.dim() != 2 or a.shape[0] < n or a.shape[1] < K1 or (a.shape[1] > 1 and a.stride(0) != 1):
+            raise ValueError(f"a must be a column-major 2-D tensor with at least {n} rows and {K1} columns")
+        _need_device(a, "a", q.dtype, 1)
+        _need_flat(tau, "tau", q.dtype, K1)
+        _check_q(q, n, nev, q.dtype)
+    elif a.dim() != 2:
+        raise ValueError("a must be 2-D")
     lda = a.stride(1) if a.shape[1] > 1 else max(a.shape[0], 1)
     ldq, _ = _q_layout(q, n)
     L = _native.load()
@@ -177,6 +231,7 @@ def trans_ev_tridi_to_band_noalloc(hh_v, hh_tau, n: int, nbw: int, nev: int, q, 
     fixed 32 MiB array per device, and concurrent calls race on it). Raises
     TbbtError (ENOTSUP) for problems whose scratch does not fit."""
     cplx = _is_complex_dtype(q)
+    _check_store_and_q(hh_v, hh_tau, n, nbw, nev, q, cplx)
     if ldq is None:
         ldq, _ = _q_layout(q, n)
     st = _native.load().tbbt_trans_ev_tridi_to_band_noalloc(
@@ -219,12 +274,22 @@ class Plan:
         _check(st, "tbbt_plan_create")
 
     def set_reflectors(self, hh_v, hh_tau, stream=None):
+        import torch
+
+        K = num_reflectors(self.n, self.nbw, self.complex)
+        if K > 0:
+            dt = torch.complex128 if self.complex else torch.float64
+            _need_flat(hh_v, "hh_v", dt, K * self.nbw)
+            _need_flat(hh_tau, "hh_tau", dt, K)
         st = _native.load().tbbt_plan_set_reflectors(
             self._h, ctypes.c_void_p(hh_v.data_ptr() if hh_v.numel() else 0),
             ctypes.c_void_p(hh_tau.data_ptr() if hh_tau.numel() else 0), _stream_handle(stream))
         _check(st, "tbbt_plan_set_reflectors")
 
     def execute(self, q, ldq: int | None = None, stream=None):
+        import torch
+
+        _check_q(q, self.n, self.nev, torch.complex128 if self.complex else torch.float64)
         if ldq is None:
             ldq, _ = _q_layout(q, self.n)
         st = _native.load().tbbt_plan_execute(self._h, ctypes.c_void_p(q.data_ptr() if q.numel() else 0), ldq,
@@ -278,6 +343,7 @@ class Batch:
         arr = (Problem * len(problems))()
         for i, (hh_v, hh_tau, n, nbw, nev, q) in enumerate(problems):
             cplx = _is_complex_dtype(q)
+            _check_store_and_q(hh_v, hh_tau, n, nbw, nev, q, cplx)
             ldq, _ = _q_layout(q, n)
             arr[i] = Problem(COMPLEX128 if cplx else REAL64, 0, n, nbw, nev,
                              hh_v.data_ptr() if hh_v.numel() else None,
