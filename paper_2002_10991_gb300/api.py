@@ -194,6 +194,28 @@ def trans_ev_band_to_full(a, tau, n: int, nbw: int, nev: int, q, stream=None):
     return q
 
 
+def _check_host_args(hh_v, hh_tau, n: int, nbw: int, nev: int, q, cplx: bool):
+    """The host entry point copies from these buffers: host memory, the
+    problem's element type, long enough."""
+    if n < 1 or nbw < 1 or nev < 1:
+        return
+    K = num_reflectors(n, nbw, cplx)
+    want = np.complex128 if cplx else np.float64
+    for name, t, need in (("hh_v", hh_v, K * nbw), ("hh_tau", hh_tau, K), ("q", q, n * nev)):
+        if need <= 0:
+            continue
+        if isinstance(t, np.ndarray):
+            dt, size = t.dtype, t.size
+        else:
+            if t.is_cuda:
+                raise ValueError(f"{name} must be in host memory for the host entry point")
+            dt, size = np.dtype(str(t.dtype).replace("torch.", "")), t.numel()
+        if dt != want:
+            raise TypeError(f"{name} has dtype {dt}, expected {np.dtype(want)}")
+        if size < need:
+            raise ValueError(f"{name} has {size} elements, needs at least {need}")
+
+
 def trans_ev_tridi_to_band_host(hh_v, hh_tau, n: int, nbw: int, nev: int, q, ldq: int | None = None, stream=None,
                                 synchronize: bool = True):
     """The same with every array in host memory (numpy arrays or CPU
@@ -214,6 +236,7 @@ def trans_ev_tridi_to_band_host(hh_v, hh_tau, n: int, nbw: int, nev: int, q, ldq
         cplx = _is_complex_dtype(q)
         if ldq is None:
             ldq, _ = _q_layout(q, n)
+    _check_host_args(hh_v, hh_tau, n, nbw, nev, q, cplx)
     L = _native.load()
     f = L.tbbt_trans_ev_tridi_to_band_host_z if cplx else L.tbbt_trans_ev_tridi_to_band_host_d
     h = _stream_handle(stream)

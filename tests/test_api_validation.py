@@ -80,3 +80,17 @@ def test_validation_helpers_check_type_and_size():
         api._need_flat(FakeCuda(f64(4, 4).t()), "hh_v", torch.float64, 16)
     api._need_flat(FakeCuda(f64(16)), "hh_v", torch.float64, 16)  # accepted
     api._need_device(f64(0), "empty", torch.float64, 0)  # nothing to read: accepted anywhere
+
+
+def test_host_entry_point_checks_its_buffers():
+    import numpy as np
+
+    n, b, nev = 40, 4, 5
+    K = P.num_reflectors(n, b, False)
+    q = np.zeros((n, nev), order="F")
+    with pytest.raises(ValueError, match="at least"):
+        P.trans_ev_tridi_to_band_host(np.zeros(K * b - 1), np.zeros(K), n, b, nev, q)
+    with pytest.raises(TypeError):
+        P.trans_ev_tridi_to_band_host(np.zeros(K * b, np.complex128), np.zeros(K), n, b, nev, q)
+    with pytest.raises(TypeError):
+        P.trans_ev_tridi_to_band_host(f64(K * b), torch.zeros(K, dtype=torch.float32), n, b, nev, q)
