@@ -81,12 +81,31 @@ def _q_layout(q, n):
     if q.dim() != 2:
         raise ValueError("q must be 2-D (ldq >= n rows, nev columns), column-major")
     rows, nev = q.shape
-    if nev > 1 and q.stride(0) != 1:
+    if rows > 1 and q.numel() > 0 and q.stride(0) != 1:
         raise ValueError("q must be column-major (stride(0) == 1)")
     ldq = q.stride(1) if nev > 1 else max(rows, 1)
     if rows < n:
         raise ValueError("q has fewer than n rows")
     return ldq, nev
+
+
+def _resolve_ldq(q, n: int, nev: int, ldq):
+    """The leading dimension the library is given for q. It is the view's own
+    column stride: the kernels touch ldq * (nev - 1) + n elements from q's
+    first one, so an ldq larger than the stride (or a row-major view) would
+    reach past the caller's memory. An explicit ldq must agree with it."""
+    lay, cols = _q_layout(q, n)
+    if nev > 0 and cols < nev:
+        raise ValueError(f"q has {cols} columns, needs at least {nev}")
+    if ldq is None:
+        return lay
+    if ldq < max(n, 1):
+        return ldq  # the library reports a leading dimension below n
+    if nev > 1 and ldq != lay:
+        raise ValueError(f"ldq={ldq} does not match q's column stride {lay}")
+    if nev <= 1 and ldq > lay:
+        raise ValueError(f"ldq={ldq} exceeds q's {lay} rows")
+    return ldq
 
 
 def _check_q(q, n: int, nev: int, dtype):
@@ -116,8 +135,7 @@ def trans_ev_tridi_to_band(hh_v, hh_tau, n: int, nbw: int, nev: int, q, ldq: int
     tensors of dtype float64 (real symmetric) or complex128 (Hermitian)."""
     cplx = _is_complex_dtype(q)
     _check_store_and_q(hh_v, hh_tau, n, nbw, nev, q, cplx)
-    if ldq is None:
-        ldq, _ = _q_layout(q, n)
+    ldq = _resolve_ldq(q, n, nev, ldq)
     L = _native.load()
     f = L.tbbt_trans_ev_tridi_to_band_z if cplx else L.tbbt_trans_ev_tridi_to_band_d
     st = f(ctypes.c_void_p(hh_v.data_ptr() if hh_v.numel() else 0),
@@ -194,14 +212,15 @@ def trans_ev_band_to_full(a, tau, n: int, nbw: int, nev: int, q, stream=None):
     return q
 
 
-def _check_host_args(hh_v, hh_tau, n: int, nbw: int, nev: int, q, cplx: bool):
-    """The host entry point copies from these buffers: host memory, the
-    problem's element type, long enough."""
+def _check_host_args(hh_v, hh_tau, n: int, nbw: int, nev: int, q, ldq: int, cplx: bool):
+    """The host entry point copies from these buffers (and back into q, at
+    pitch ldq): host memory, the problem's element type, long enough."""
     if n < 1 or nbw < 1 or nev < 1:
         return
     K = num_reflectors(n, nbw, cplx)
     want = np.complex128 if cplx else np.float64
-    for name, t, need in (("hh_v", hh_v, K * nbw), ("hh_tau", hh_tau, K), ("q", q, n * nev)):
+    q_need = ldq * (nev - 1) + n
+    for name, t, need in (("hh_v", hh_v, K * nbw), ("hh_tau", hh_tau, K), ("q", q, q_need)):
         if need <= 0:
             continue
         if isinstance(t, np.ndarray):
@@ -228,15 +247,25 @@ def trans_ev_tridi_to_band_host(hh_v, hh_tau, n: int, nbw: int, nev: int, q, ldq
 
     if isinstance(q, np.ndarray):
         cplx = np.iscomplexobj(q)
-        if ldq is None:
-            ldq = q.shape[0]
+        if q.ndim != 2:
+            raise ValueError("q must be 2-D (ldq >= n rows, nev columns), Fortran-ordered")
         if not q.flags.f_contiguous:
             raise ValueError("q must be Fortran-ordered")
+        rows, cols = q.shape
+        if rows < n or (nev > 0 and cols < nev):
+            raise ValueError(f"q must be at least {n} x {nev}")
+        if ldq is None:
+            ldq = max(rows, 1)
+        elif ldq >= max(n, 1) and ldq != max(rows, 1) and nev > 1:
+            raise ValueError(f"ldq={ldq} does not match q's leading dimension {rows}")
+        elif ldq > max(rows, 1):
+            raise ValueError(f"ldq={ldq} exceeds q's {rows} rows")
     else:
         cplx = _is_complex_dtype(q)
-        if ldq is None:
-            ldq, _ = _q_layout(q, n)
-    _check_host_args(hh_v, hh_tau, n, nbw, nev, q, cplx)
+        if q.is_cuda:
+            raise ValueError("q must be in host memory for the host entry point")
+        ldq = _resolve_ldq(q, n, nev, ldq)
+    _check_host_args(hh_v, hh_tau, n, nbw, nev, q, ldq, cplx)
     L = _native.load()
     f = L.tbbt_trans_ev_tridi_to_band_host_z if cplx else L.tbbt_trans_ev_tridi_to_band_host_d
     h = _stream_handle(stream)
@@ -255,8 +284,7 @@ def trans_ev_tridi_to_band_noalloc(hh_v, hh_tau, n: int, nbw: int, nev: int, q, 
     TbbtError (ENOTSUP) for problems whose scratch does not fit."""
     cplx = _is_complex_dtype(q)
     _check_store_and_q(hh_v, hh_tau, n, nbw, nev, q, cplx)
-    if ldq is None:
-        ldq, _ = _q_layout(q, n)
+    ldq = _resolve_ldq(q, n, nev, ldq)
     st = _native.load().tbbt_trans_ev_tridi_to_band_noalloc(
         COMPLEX128 if cplx else REAL64, ctypes.c_void_p(hh_v.data_ptr() if hh_v.numel() else 0),
         ctypes.c_void_p(hh_tau.data_ptr() if hh_tau.numel() else 0), n, nbw, nev,
@@ -313,8 +341,7 @@ class Plan:
         import torch
 
         _check_q(q, self.n, self.nev, torch.complex128 if self.complex else torch.float64)
-        if ldq is None:
-            ldq, _ = _q_layout(q, self.n)
+        ldq = _resolve_ldq(q, self.n, self.nev, ldq)
         st = _native.load().tbbt_plan_execute(self._h, ctypes.c_void_p(q.data_ptr() if q.numel() else 0), ldq,
                                               _stream_handle(stream))
         _check(st, "tbbt_plan_execute")

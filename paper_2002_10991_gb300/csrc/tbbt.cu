@@ -82,6 +82,40 @@ size_t smem_bytes_for(tbbt_dtype dt, int32_t b, int32_t G, int32_t NB) {
   return (size_t)ring_rows_for(b, G, NB) * 32 * es + (size_t)G * 2 * NB * round_even(b) * es;
 }
 
+// Register-window width of the apply kernel for a problem: real b = 32 or 64
+// keep each column's window in registers, complex data take a lane pair per
+// column (-1), other widths the shared-memory window (0).
+int32_t window_width(tbbt_dtype dt, int64_t nbw) {
+  if (dt == TBBT_COMPLEX128) return -1;
+  return (nbw == 32 || nbw == 64) ? (int32_t)nbw : 0;
+}
+
+// Threads of one apply block: a warp per sweep (two for lane pairs).
+int32_t apply_threads(int32_t G, int32_t bw) { return G * 32 * (bw < 0 ? 2 : 1); }
+
+// Launch geometry: the requested sweeps per block (wantG) and stages per
+// step (wantNB), lowered until the block's ring and reflector buffers fit in
+// shared memory. Returns false if nothing fits.
+bool fit_geometry(tbbt_dtype dt, int32_t nbw, int32_t bw, int32_t wantG, int32_t wantNB, int32_t *G_out,
+                  int32_t *NB_out) {
+  if (bw != 0 && wantG > 8) wantG = 8;  // register window: 256 threads; lane pairs: 512
+  if (wantG > 16) wantG = 16;
+  int32_t G = wantG, NB = wantNB;
+  if (NB > 4 * G) NB = 4 * G;  // the row prefetch holds at most 4 elements per thread
+  while (smem_bytes_for(dt, nbw, G, NB) > (size_t)kMaxSmem) {
+    if (G > 4 || (NB <= 2 && G > 1))
+      --G;
+    else if (NB > 2)
+      NB /= 2;
+    else
+      break;
+  }
+  if (smem_bytes_for(dt, nbw, G, NB) > (size_t)kMaxSmem) return false;
+  *G_out = G;
+  *NB_out = NB;
+  return true;
+}
+
 tbbt_status check_shape(int64_t n, int64_t nbw, int64_t nev) {
   if (n < 0 || n > (int64_t)1 << 30) return TBBT_EINVAL;
   if (nbw < 1 || nbw > kMaxBand) return TBBT_EINVAL;
@@ -410,27 +444,15 @@ tbbt_status tbbt_plan_create(tbbt_plan **plan, tbbt_dtype dtype, int64_t n, int6
   p->ldv = round_even((int32_t)nbw);
   // real data with b = 32 or 64 keep each column's window in registers
   // complex data: two warps per sweep (a lane pair per column)
-  p->bw = (dtype == TBBT_REAL64 && (nbw == 32 || nbw == 64)) ? (int32_t)nbw : (dtype == TBBT_COMPLEX128 ? -1 : 0);
+  p->bw = window_width(dtype, nbw);
   // launch geometry: most sweeps per block that fit in shared memory
   // Default: 4 sweeps per block (one warp per SM sub-partition) and 8 stages
   // per step; two such blocks share an SM when they fit, so one block's
   // pipeline fill is covered by the other. Block widths that are not a
   // multiple of 4 load the sub-partitions unevenly and are slower.
-  int32_t wantG = opt && opt->sweeps_per_block > 0 ? opt->sweeps_per_block : 4;
-  if (p->bw != 0 && wantG > 8) wantG = 8;  // register window: 256 threads; lane pairs: 512
-  int32_t wantNB = opt && opt->stages_per_step > 0 ? opt->stages_per_step : 8;
-  if (wantG > 16) wantG = 16;
-  int32_t G = wantG, NB = wantNB;
-  if (NB > 4 * G) NB = 4 * G;  // the row prefetch holds at most 4 elements per thread
-  while (smem_bytes_for(dtype, (int32_t)nbw, G, NB) > (size_t)kMaxSmem) {
-    if (G > 4 || (NB <= 2 && G > 1))
-      --G;
-    else if (NB > 2)
-      NB /= 2;
-    else
-      break;
-  }
-  if (smem_bytes_for(dtype, (int32_t)nbw, G, NB) > (size_t)kMaxSmem) {
+  int32_t G = 0, NB = 0;
+  if (!fit_geometry(dtype, (int32_t)nbw, p->bw, opt && opt->sweeps_per_block > 0 ? opt->sweeps_per_block : 4,
+                    opt && opt->stages_per_step > 0 ? opt->stages_per_step : 8, &G, &NB)) {
     delete p;
     return TBBT_ENOTSUP;
   }
@@ -488,7 +510,7 @@ tbbt_status tbbt_plan_create(tbbt_plan **plan, tbbt_dtype dtype, int64_t n, int6
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return fail(TBBT_ECUDA);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_fn(dtype, p->bw), G * 32 * (p->bw < 0 ? 2 : 1),
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_fn(dtype, p->bw), apply_threads(G, p->bw),
                                                       p->smem);
     if (e != cudaSuccess || per_sm < 1) return fail(TBBT_ECUDA);
     int64_t resident = (int64_t)sms * per_sm;
@@ -575,7 +597,7 @@ tbbt_status tbbt_plan_execute(tbbt_plan *p, void *q, int64_t ldq, void *stream) 
   TBBT_CUDA_TRY(cudaMemsetAsync(p->d_flags, 0x7f, sizeof(int) * (size_t)p->units, s));
   TBBT_CUDA_TRY(cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned), s));
   unsigned blocks = (unsigned)p->grid;
-  apply_fn(p->dtype, p->bw)<<<blocks, p->G * 32 * (p->bw < 0 ? 2 : 1), p->smem, s>>>(a);
+  apply_fn(p->dtype, p->bw)<<<blocks, apply_threads(p->G, p->bw), p->smem, s>>>(a);
   TBBT_CUDA_TRY(cudaGetLastError());
   return TBBT_OK;
 }
@@ -734,8 +756,8 @@ tbbt_status tbbt_release_cache(void) {
 // the host-device synchronisation implied by cudaMalloc/cudaFree is not
 // acceptable (the cost the paper avoids by pre-allocating outside the work
 // loop, Sec. 3.1), or it must never fail with out-of-memory at run time.
-// This variant runs the same kernels as the plan path but keeps all of their
-// scratch -- the sweep-major store, the stage-offset table, the per-unit
+// This variant runs the same kernel instances, with the same default launch
+// geometry, as the plan path but keeps all of their scratch -- the sweep-major store, the stage-offset table, the per-unit
 // progress flags and the claim counter -- in one fixed array that exists
 // from the moment the library's device code is loaded.
 // ---------------------------------------------------------------------------
@@ -785,8 +807,10 @@ tbbt_status noalloc_device(int *dev_out, NoAllocDevice **out) {
     }
     int sms = 0;
     TBBT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    TBBT_CUDA_TRY(allow_max_dynamic_smem(tbbt::apply_kernel<double, 0>));
-    TBBT_CUDA_TRY(allow_max_dynamic_smem(tbbt::apply_kernel<zdouble, 0>));
+    TBBT_CUDA_TRY(allow_max_dynamic_smem(apply_fn(TBBT_REAL64, 0)));
+    TBBT_CUDA_TRY(allow_max_dynamic_smem(apply_fn(TBBT_REAL64, 32)));
+    TBBT_CUDA_TRY(allow_max_dynamic_smem(apply_fn(TBBT_REAL64, 64)));
+    TBBT_CUDA_TRY(allow_max_dynamic_smem(apply_fn(TBBT_COMPLEX128, -1)));
     d.scratch = (unsigned char *)ptr;
     d.sms = sms;
     d.ready = 1;
@@ -804,17 +828,12 @@ tbbt_status noalloc_launch(NoAllocDevice &d, tbbt_dtype dtype, const void *hh_v,
   if (K == 0 || nev == 0) return TBBT_OK;
   const size_t es = elem_size(dtype);
   const int32_t ldv = round_even((int32_t)nbw);
-  // launch geometry: up to 8 sweeps per block and 8 stages per step, as
-  // many as fit in shared memory
-  int32_t G = 8, NB = 8;
-  while (smem_bytes_for(dtype, (int32_t)nbw, G, NB) > (size_t)kMaxSmem && (G > 1 || NB > 1)) {
-    if (G > 4 || (NB <= 2 && G > 1))
-      --G;
-    else
-      NB = NB > 1 ? NB / 2 : 1;
-  }
+  // the kernel instance and default launch geometry of the plan path
+  const int32_t bw = window_width(dtype, nbw);
+  int32_t G = 0, NB = 0;
+  if (!fit_geometry(dtype, (int32_t)nbw, bw, 4, 8, &G, &NB)) return TBBT_ENOTSUP;
   const size_t smem = smem_bytes_for(dtype, (int32_t)nbw, G, NB);
-  if (smem > (size_t)kMaxSmem) return TBBT_ENOTSUP;
+  const ApplyFn kern = apply_fn(dtype, bw);
   const int32_t strips = (int32_t)((nev + 31) / 32);
   const int32_t epochs = (g.num_sweeps() + G - 1) / G;
   const int64_t units = (int64_t)strips * epochs;
@@ -830,7 +849,7 @@ tbbt_status noalloc_launch(NoAllocDevice &d, tbbt_dtype dtype, const void *hh_v,
   unsigned *counter = reinterpret_cast<unsigned *>(base + b_store + b_off + b_flags);
 
   int per_sm = 0;
-  TBBT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tbbt::apply_kernel<T, 0>, G * 32, smem));
+  TBBT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, apply_threads(G, bw), smem));
   if (per_sm < 1) return TBBT_ENOTSUP;
 
   fill_stage_offsets_kernel<<<(unsigned)((n + 1 + 255) / 256), 256, 0, s>>>(off, g);
@@ -865,7 +884,7 @@ tbbt_status noalloc_launch(NoAllocDevice &d, tbbt_dtype dtype, const void *hh_v,
   a.withhold = -1;
   const int64_t resident = (int64_t)d.sms * per_sm;
   const unsigned grid = (unsigned)(units < resident ? units : resident);
-  tbbt::apply_kernel<T, 0><<<grid, G * 32, smem, s>>>(a);
+  kern<<<grid, apply_threads(G, bw), smem, s>>>(a);
   TBBT_CUDA_TRY(cudaGetLastError());
   return TBBT_OK;
 }

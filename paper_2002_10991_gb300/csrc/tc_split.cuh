@@ -19,8 +19,9 @@
 //    K = window rows: one instruction per digit of Z and K step covers every V'
 //    slice it pairs with, writing each slice into the TMEM columns of its
 //    level (level l = i + k of the 0-based digit indices, 32 columns each).
-//    The digits of Z are produced into two alternating shared-memory buffers
-//    while the tensor core consumes the previous one.
+//    The math warps write the six digit slices of Z into tensor memory
+//    (tcgen05.st) as the A operand of these MMAs, one ready barrier per
+//    digit, so the tensor core starts on a digit as soon as it is complete.
 //  * W is combined per column by the thread that owns the column (no
 //    shuffles), normalised, split into digits (the A operand of GEMM2).
 //  * GEMM2 corr^T = W^T U'^T runs per part of 32 rows (M = 128, N = 32 *

@@ -94,3 +94,44 @@ def test_host_entry_point_checks_its_buffers():
         P.trans_ev_tridi_to_band_host(np.zeros(K * b, np.complex128), np.zeros(K), n, b, nev, q)
     with pytest.raises(TypeError):
         P.trans_ev_tridi_to_band_host(f64(K * b), torch.zeros(K, dtype=torch.float32), n, b, nev, q)
+
+
+def test_leading_dimension_must_match_the_view():
+    from paper_2002_10991_gb300 import api
+
+    n, nev = 40, 5
+    q = f64(nev, n).t()  # column-major view, column stride n
+    assert api._resolve_ldq(q, n, nev, None) == n
+    assert api._resolve_ldq(q, n, nev, n) == n
+    with pytest.raises(ValueError, match="column stride"):
+        api._resolve_ldq(q, n, nev, n + 8)  # would reach 8 * (nev - 1) elements past q
+    with pytest.raises(ValueError, match="column-major"):
+        api._resolve_ldq(f64(n, nev), n, nev, n)  # row-major storage
+    with pytest.raises(ValueError, match="column-major"):
+        api._resolve_ldq(f64(n, 3)[:, :1], n, 1, None)  # one column of a row-major matrix
+    with pytest.raises(ValueError, match="columns"):
+        api._resolve_ldq(f64(nev - 1, n).t(), n, nev, None)
+    with pytest.raises(ValueError, match="exceeds"):
+        api._resolve_ldq(f64(1, n).t(), n, 1, n + 1)
+    padded = f64(nev, n + 3).t()[:n]  # ldq = n + 3 > n rows of the view
+    assert api._resolve_ldq(padded, n, nev, None) == n + 3
+
+
+def test_host_entry_point_checks_the_leading_dimension():
+    import numpy as np
+
+    n, b, nev = 40, 4, 5
+    K = P.num_reflectors(n, b, False)
+    v, tau = np.zeros(K * b), np.zeros(K)
+    q = np.zeros((n, nev), order="F")
+    with pytest.raises(ValueError, match="leading dimension"):
+        P.trans_ev_tridi_to_band_host(v, tau, n, b, nev, q, ldq=n + 8)  # the copies would overrun q
+    with pytest.raises(ValueError, match="2-D"):
+        P.trans_ev_tridi_to_band_host(v, tau, n, b, nev, np.zeros(n * nev))
+    with pytest.raises(ValueError, match="Fortran"):
+        P.trans_ev_tridi_to_band_host(v, tau, n, b, nev, np.zeros((n, nev)))
+    with pytest.raises(ValueError, match="at least"):
+        P.trans_ev_tridi_to_band_host(v, tau, n, b, nev, np.zeros((n, nev - 1), order="F"))
+    with pytest.raises(ValueError, match="column stride"):
+        P.trans_ev_tridi_to_band_host(torch.from_numpy(v), torch.from_numpy(tau), n, b, nev, f64(nev, n).t(),
+                                      ldq=n + 1)

@@ -59,6 +59,32 @@ def test_noalloc_matches_allocating_entry_point_twice_in_a_row(P, cplx):
             assert np.all(np.isnan(tail))
 
 
+@pytest.mark.parametrize("cplx", [False, True])
+def test_noalloc_small_call_then_larger_call(P, cplx):
+    # the second problem needs more store, stage offsets and progress flags
+    # than the first left in the array: stale tails must not leak into it
+    big = (1800, 64, 500, 13, 2) if cplx else (2000, 64, 500, 13, 2)
+    for n, b, nev, seed, pad in [(1000, 32, 129, 11, 0), big]:
+        ref, got, tail = run_both(P, n, b, nev, cplx, seed, pad)
+        assert np.abs(got - ref).max() <= TOL
+        if pad:
+            assert np.all(np.isnan(tail))
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_noalloc_matches_the_oracle(P, cplx):
+    import oracle
+
+    n, b, nev, seed = 700, 64, 150, 17
+    v, tau = I.synthetic_store(n, b, seed, cplx)
+    X = I.eigvec_block(n, nev, seed + 1, cplx)
+    Zo = oracle.back_transform(v, tau, n, b, np.asfortranarray(X.copy()))
+    q = col_major(X)
+    P.trans_ev_tridi_to_band_noalloc(torch.from_numpy(v).cuda(), torch.from_numpy(tau).cuda(), n, b, nev, q)
+    P.stream_check()
+    assert np.abs(q.cpu().numpy() - Zo).max() <= TOL
+
+
 def test_noalloc_rejects_problems_beyond_its_scratch(P):
     n, b, nev = 6000, 64, 64  # sweep-major store alone is about 140 MB
     v, tau = I.synthetic_store(n, b, 1, False)
