@@ -1,16 +1,23 @@
 """Benchmark of the tridiagonal -> band eigenvector back-transformation (Eq. 6d).
 
-Workload: real symmetric, n = 8192, semi-bandwidth 64, nev = 4096 lowest
-eigenvectors (the paper's plain FP64 method at a DFT-like size). One step =
-the whole hot path on one batch: re-lay the reflector store (K = 528,128
-reflectors) and apply it to the 8192 x 4096 eigenvector block. Inputs are
-seeded and synthetic (unitary Householder reflectors with the exact store
-geometry, N(0, 1/n) eigenvector block); both exceed the 129 MB L2.
+Default workload: real symmetric, n = 32768, semi-bandwidth 64, nev = 9830
+lowest eigenvectors (DFT-like band; the largest single-GPU configuration,
+the one the precision form is quoted on). One step = the whole hot path on
+one batch: re-lay the reflector store (K = 8,403,968 reflectors) and apply it
+to the 32768 x 9830 eigenvector block with the FP64 kernel. Inputs are seeded
+and synthetic (unitary Householder reflectors with the exact store geometry,
+N(0, 1/n) eigenvector block); both exceed the 129 MB L2.
 
 Metric: algorithmic TFLOP/s = 4 * nev * sum_k L_k flops per step (Eq. 8:
 a length-L dot product and a length-L update per reflector and column)
 divided by device time. Roofline: the apply kernel is FP64-ALU bound
-(arithmetic intensity ~700 flop/byte, far above the FP64 ridge of ~0.2).
+(arithmetic intensity ~2000 flop/byte, far above the FP64 ridge of ~0.2); its
+peak is the FP64 rate measured by the library's probe in the same run, at the
+clock sampled while the kernel ran. The same JSON line carries the split-
+precision (BF16 tensor-core) form on the same inputs (speed-up over FP64 and
+its error against the oracle), and the other configurations as sub-objects:
+complex n = 20000, the 64-problem batch against sequential launches, and
+n = 512.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -39,7 +46,9 @@ if ROOT not in sys.path:
 from paper_2002_10991_gb300 import inputs as I  # noqa: E402
 
 METRIC = "eigvec back-transform TFLOP/s,% FP64 peak; mixed vs FP64 speedup at set resid"
-WORKLOAD = "real-n8192-b64-dft"
+WORKLOAD = "real-n32768-b64-dft"
+# the other configurations, measured as sub-objects of the default line
+EXTRA_WORKLOADS = ("complex-n20000-b64-dft", "batch-64-mixed", "real-n512-b32-uniform")
 
 # FP64 peak of a GB300: 152 SMs x 2 DFMA per clock x 2 flops at the 2070 MHz
 # maximum SM clock (a DFMA microbenchmark measured 1.198 TFLOP/s at ~2000 MHz,
@@ -252,15 +261,15 @@ def bulge_bench(args):
     print(json.dumps(line), flush=True)
 
 
-def batch_bench(args):
+def batch_measure(steps: int, autotune: bool = False):
     """The batched form: 64 problems (N uniform in [1000, 6000], nev = N/2,
     b = 32, even p real, odd p complex) in one persistent graph-replayed
-    launch, against the same problems as 64 sequential plan launches."""
+    launch, against the same problems as 64 sequential plan launches. Returns
+    a dict of the measurements (inputs built and freed here)."""
     import torch
 
     import paper_2002_10991_gb300 as P
 
-    torch.cuda.set_device(0)
     specs = I.batch_workload()
     probs, flops = [], 0
     for s in specs:
@@ -271,20 +280,20 @@ def batch_bench(args):
                       torch.from_numpy(X.T.copy()).cuda().t()))
         flops += (16 if c else 4) * nev * int(I.store_lengths(n, b, c).sum())
     t0 = time.perf_counter()
-    batch = P.Batch(probs, autotune=args.autotune, autotune_cache=os.environ.get("TBBT_AUTOTUNE_CACHE"))
+    batch = P.Batch(probs, autotune=autotune, autotune_cache=os.environ.get("TBBT_AUTOTUNE_CACHE"))
     create_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
     batch.execute()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(0) as clocks:
+    with ClockSampler(torch.cuda.current_device()) as clocks:
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             batch.execute()
         e1.record(stream)
         torch.cuda.synchronize()
     P.stream_check()
-    batched_ms = e0.elapsed_time(e1) / args.steps
+    batched_ms = e0.elapsed_time(e1) / steps
     # the same problems, one plain plan launch after another
     plans = [P.Plan(bool(s["complex_"]), s["n"], s["b"], s["nev"]) for s in specs]
     for pl, (dv, dt, n, b, nev, q) in zip(plans, probs):
@@ -292,33 +301,47 @@ def batch_bench(args):
         pl.execute(q)
     torch.cuda.synchronize()
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         for pl, (dv, dt, n, b, nev, q) in zip(plans, probs):
             pl.set_reflectors(dv, dt)
             pl.execute(q)
     e1.record(stream)
     torch.cuda.synchronize()
     P.stream_check()
-    seq_ms = e0.elapsed_time(e1) / args.steps
-    value = flops / (batched_ms * 1e-3) / 1e12
-    line = {
-        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": 1,
-        "ms_per_step": batched_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64+c128", "data": "synthetic",
-        "config": {"workload": BATCH_WORKLOAD, "problems": len(specs), "n_range": [min(s["n"] for s in specs),
-                   max(s["n"] for s in specs)], "nbw": 32, "nev": "n/2", "complex_problems": sum(s["complex_"] for s in specs),
-                   "store": "seeded synthetic unitary reflectors", "flops_per_step": flops},
-        "batched": {"ms": batched_ms, "tflops": value, "launch": batch.info(), "create_s": create_s},
-        "sequential": {"ms": seq_ms, "tflops": flops / (seq_ms * 1e-3) / 1e12, "launches_per_step": 2 * len(specs)},
-        "speedup_vs_sequential": seq_ms / batched_ms,
-        "roofline": {"bound": "alu", "achieved": value, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": value / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "tbbt::batch_kernel"},
-        "clocks": clocks.summary(), "gpu_launches": 1 + len(specs),
-    }
-    print(json.dumps(line), flush=True)
+    seq_ms = e0.elapsed_time(e1) / steps
+    info = batch.info()
     batch.close()
     for pl in plans:
         pl.close()
+    value = flops / (batched_ms * 1e-3) / 1e12
+    return {
+        "workload": BATCH_WORKLOAD, "problems": len(specs),
+        "n_range": [min(s["n"] for s in specs), max(s["n"] for s in specs)], "nbw": 32, "nev": "n/2",
+        "complex_problems": sum(s["complex_"] for s in specs), "flops_per_step": flops, "steps": steps,
+        "batched": {"ms": batched_ms, "tflops": value, "launch": info, "create_s": create_s},
+        "sequential": {"ms": seq_ms, "tflops": flops / (seq_ms * 1e-3) / 1e12, "launches_per_step": 2 * len(specs)},
+        "speedup_vs_sequential": seq_ms / batched_ms, "clocks": clocks.summary(),
+    }
+
+
+def batch_bench(args):
+    import torch
+
+    torch.cuda.set_device(0)
+    m = batch_measure(args.steps, args.autotune)
+    value = m["batched"]["tflops"]
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": 1,
+        "ms_per_step": m["batched"]["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64+c128", "data": "synthetic",
+        "config": {k: m[k] for k in ("workload", "problems", "n_range", "nbw", "nev", "complex_problems",
+                                     "flops_per_step")},
+        "batched": m["batched"], "sequential": m["sequential"], "speedup_vs_sequential": m["speedup_vs_sequential"],
+        "roofline": {"bound": "alu", "achieved": value, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": value / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "tbbt::batch_kernel"},
+        "clocks": m["clocks"], "gpu_launches": 1 + 64,
+    }
+    print(json.dumps(line), flush=True)
 
 
 def csrc_hash() -> str:
@@ -331,14 +354,18 @@ def csrc_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
+def recorded_traffic(workload: str):
+    """DRAM bytes of one apply-kernel launch of ``workload`` from the ncu
+    record, or None if there is none for the current kernel sources."""
     try:
-        rec = json.load(open(TRAFFIC_FILE))
+        recs = json.load(open(TRAFFIC_FILE))["records"]
     except Exception:
         return None
-    if rec.get("csrc_hash") != csrc_hash():
-        return None
-    return rec.get("bytes_per_launch")
+    h = csrc_hash()
+    for rec in recs:
+        if rec.get("workload") == workload and rec.get("csrc_hash") == h:
+            return rec.get("bytes_per_launch")
+    return None
 
 
 class ClockSampler:
@@ -408,6 +435,14 @@ def workload_inputs(name: str):
     return w, v, tau, X, sum_l, flops
 
 
+def sample_cols(w, sum_l, flops_target: float, lo: int = 16) -> int:
+    """Columns of a host sample worth about ``flops_target`` oracle flops
+    (a multiple of 16, at least ``lo``, at most nev)."""
+    per_col = (16 if w["complex_"] else 4) * max(sum_l, 1)
+    c = int(flops_target / per_col) // 16 * 16
+    return int(min(max(c, lo), w["nev"]))
+
+
 def cpu_sample(v, tau, X, w, ncols: int, seed: int = 1):
     """Columns of the workload the oracle back-transforms on the host."""
     rng = np.random.default_rng(seed)
@@ -445,14 +480,16 @@ def dist_setup():
 
 
 def reference_arm(args, world, rank):
-    """The oracle timed on the host cores (rank 0 only)."""
+    """The oracle timed on the host cores (rank 0 only), each step a column
+    sample of the workload worth about a second of the host's work."""
     if rank != 0:
         return
     w, v, tau, X, sum_l, flops_full = workload_inputs(WORKLOAD)
-    ncols = args.ref_cols
+    ncols = args.ref_cols if args.ref_cols else sample_cols(w, sum_l, 6e10)
     cols, Xs = cpu_sample(v, tau, X, w, ncols)
     fl = (16 if w["complex_"] else 4) * len(cols) * sum_l
-    for _ in range(args.warmup_ref):
+    warm = args.warmup if args.warmup_ref is None else args.warmup_ref
+    for _ in range(warm):
         run_oracle_sample(v, tau, w, Xs)
     times, cores = [], 1
     for _ in range(args.steps):
@@ -462,7 +499,7 @@ def reference_arm(args, world, rank):
     value = fl * len(times) / total / 1e12
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup_ref, "ms_per_step": 1e3 * total / len(times),
+        "steps": args.steps, "warmup": warm, "ms_per_step": 1e3 * total / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype_name(w), "data": "synthetic",
         "config": config_dict(w, "host cores; oracle sample"),
         "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
@@ -480,8 +517,8 @@ def dtype_name(w):
     return "c128" if w["complex_"] else "f64"
 
 
-def config_dict(w, note=""):
-    return {"workload": WORKLOAD, "n": w["n"], "nbw": w["b"], "nev": w["nev"],
+def config_dict(w, note="", name=None):
+    return {"workload": name or WORKLOAD, "n": w["n"], "nbw": w["b"], "nev": w["nev"],
             "dtype": "complex128" if w["complex_"] else "real64",
             "store": "seeded synthetic unitary reflectors, canonical store layout",
             "x": "seeded N(0,1/n) eigenvector block",
@@ -490,23 +527,167 @@ def config_dict(w, note=""):
             "parallelism": "replicas", "note": note}
 
 
+# ---------------------------------------------------------------------------
+# the FP64 roofline's denominator, measured in the same run
+# ---------------------------------------------------------------------------
+
+def fp64_probe(device: int, kind: int, warps_per_sm: int = 32, seconds: float = 0.4, repeats: int = 3):
+    """Rate of the library's FP64 probe (kind 0: FMA chains, kind 1: FP64
+    mma.sync m8n8k4) with ``warps_per_sm`` resident warps per SM, with the SM
+    clock sampled while it runs."""
+    import ctypes
+
+    import torch
+
+    from paper_2002_10991_gb300 import _native
+
+    L = _native.load()
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    threads = 256 if warps_per_sm >= 8 else 32 * warps_per_sm
+    blocks = sms * max(warps_per_sm * 32 // threads, 1)
+    sink = torch.empty(blocks * threads, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    h = ctypes.c_void_p(int(stream.cuda_stream))
+    fl = ctypes.c_double()
+
+    def run(iters):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = L.tbbt_fp64_probe(kind, blocks, threads, iters, ctypes.c_void_p(sink.data_ptr()), ctypes.byref(fl), h)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if st != 0:
+            raise RuntimeError(f"tbbt_fp64_probe failed with status {st}")
+        return e0.elapsed_time(e1), fl.value
+
+    iters = 200
+    ms, _ = run(iters)
+    iters = max(iters, int(iters * seconds * 1e3 / max(ms, 1e-3)))
+    best, flops = None, 0.0
+    with ClockSampler(device) as clocks:
+        for _ in range(repeats):
+            ms, flops = run(iters)
+            best = ms if best is None else min(best, ms)
+    cs = clocks.summary()
+    tf = flops / (best * 1e-3) / 1e12
+    return {"kind": ("fma", "mma")[kind], "tflops": tf, "warps_per_sm": warps_per_sm, "ms": best,
+            "sm_mhz": cs["sm_mhz"], "reasons": cs["reasons"],
+            "flop_per_clk_per_sm": tf * 1e12 / (sms * cs["sm_mhz"] * 1e6) if cs["sm_mhz"] else None}
+
+
+def fp64_peak(device: int):
+    """The FP64 peak of this device: the faster of the two probes (FMA chains
+    and FP64 tensor-core products), with the clock it was taken at."""
+    runs = [fp64_probe(device, 0), fp64_probe(device, 1)]
+    best = max(runs, key=lambda r: r["tflops"])
+    return best, runs
+
+
+def peak_at_clock(probe: dict, sm_mhz):
+    """The probe's rate scaled to the clock a kernel ran at (the FP64 rate is
+    proportional to the SM clock)."""
+    if probe.get("sm_mhz") and sm_mhz:
+        return probe["tflops"] * sm_mhz / probe["sm_mhz"]
+    return probe["tflops"]
+
+
+def fp64_peak_bench(args):
+    """The probes over a range of resident warps per SM (one JSON line)."""
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_2002_10991_gb300 import _native
+
+    _native.load()
+    runs = [fp64_probe(0, kind, wps, seconds=0.5) for kind in (0, 1) for wps in (4, 8, 16, 32, 64)]
+    best = max(runs, key=lambda r: r["tflops"])
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    line = {"metric": "FP64 peak (probe)", "value": best["tflops"], "unit": "TFLOP/s", "n_gpus": 1,
+            "steps": 3, "warmup": 1, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "fp64-peak", "sms": sms}, "best": best, "runs": runs,
+            "derived_at_max_clock": FP64_PEAK_TFLOPS}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# one FP64 configuration: time, parity on a column sample, rate
+# ---------------------------------------------------------------------------
+
+def measure_fp64(name: str, steps: int, warmup: int, parity_cols: int = 8):
+    """The plain FP64 path on one named workload: re-layout + apply per step,
+    CUDA events on the calling stream, parity of a column sample against the
+    oracle. Returns a dict (inputs built and freed here)."""
+    import torch
+
+    import paper_2002_10991_gb300 as P
+
+    w, v, tau, X, sum_l, flops = workload_inputs(name)
+    n, b, nev, cplx = w["n"], w["b"], w["nev"], w["complex_"]
+    dv, dt = torch.from_numpy(v).cuda(), torch.from_numpy(tau).cuda()
+    q = torch.from_numpy(X.T.copy()).cuda().t()
+    plan = P.Plan(cplx, n, b, nev)
+    cols, Xs = cpu_sample(v, tau, X, w, parity_cols, seed=3)
+    plan.set_reflectors(dv, dt)
+    plan.execute(q)
+    P.stream_check()
+    gpu_cols = q[:, torch.from_numpy(cols).cuda()].cpu().numpy()
+    for _ in range(warmup):
+        plan.set_reflectors(dv, dt)
+        plan.execute(q)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for k in range(steps):
+            plan.set_reflectors(dv, dt)
+            ev[k][0].record(stream)
+            plan.execute(q)
+            ev[k][1].record(stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    P.stream_check()
+    ms = t0.elapsed_time(t1) / steps
+    apply_ms = sum(a.elapsed_time(z) for a, z in ev) / steps
+    info = plan.info()
+    plan.close()
+    del q, dv, dt
+    Zo, cpu_s, cores = run_oracle_sample(v, tau, w, Xs)
+    return {"workload": name, "n": n, "nbw": b, "nev": nev, "dtype": dtype_name(w), "steps": steps,
+            "warmup": warmup, "ms_per_step": ms, "apply_ms_avg": apply_ms,
+            "tflops": flops / (ms * 1e-3) / 1e12, "apply_tflops": flops / (apply_ms * 1e-3) / 1e12,
+            "flops_per_step": flops, "launch": info, "clocks": clocks.summary(),
+            "parity": {"max_abs_err_vs_oracle": float(np.abs(Zo - gpu_cols).max()), "columns": len(cols)},
+            "kernel": "tbbt::apply_kernel<zdouble, -1>" if cplx else
+            f"tbbt::apply_kernel<double, {b if b in (32, 64) else 0}>"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-cols", type=int, default=512, help="columns in the CPU-baseline sample")
-    ap.add_argument("--ref-cols", type=int, default=256, help="columns per step of the reference arm")
-    ap.add_argument("--warmup-ref", type=int, default=1)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-cols", type=int, default=0,
+                    help="columns in the CPU-baseline sample (0: about 5e11 oracle flops' worth)")
+    ap.add_argument("--ref-cols", type=int, default=0,
+                    help="columns per step of the reference arm (0: about 6e10 oracle flops' worth)")
+    ap.add_argument("--warmup-ref", type=int, default=None, help="reference arm warm-ups (default: --warmup)")
+    ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--split-steps", type=int, default=5,
                     help="fp64 runs of real b=32/64 workloads: also time this many steps of the tcgen05 "
                          "split-precision form on the same inputs (0: skip)")
+    ap.add_argument("--extras", default="default",
+                    help="comma-separated other configurations measured into the same line "
+                         f"({', '.join(EXTRA_WORKLOADS)}); 'default' = all of them for the default workload, "
+                         "'none' = skip")
+    ap.add_argument("--extra-steps", type=int, default=2, help="timed steps of each extra configuration")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="named workload (default: the benchmark workload; others are for profiler captures, "
-                         "the batched-form measurement, the GPU bulge chase (" + ", ".join(BULGE_WORKLOADS) + ") and the band -> full "
-                         "back-transformation (" + ", ".join(B2F_WORKLOADS) + "))")
+                         "the batched-form measurement, the FP64 probe sweep (fp64-peak), the GPU bulge chase (" +
+                         ", ".join(BULGE_WORKLOADS) + ") and the band -> full back-transformation (" +
+                         ", ".join(B2F_WORKLOADS) + "))")
     ap.add_argument("--autotune", action="store_true", help="batched workload: tune the launch geometry first")
     ap.add_argument("--variant", default="fp64", choices=list(VARIANTS),
                     help="fp64: reflector-by-reflector FP64 kernel; split: WY blocks on BF16 tensor cores "
@@ -514,6 +695,10 @@ def main():
                          "on tcgen05 with accumulators in tensor memory; split forms are timed against fp64 "
                          "in the same run")
     args = ap.parse_args()
+    default_workload = args.workload == WORKLOAD
+    if args.workload == "fp64-peak":
+        fp64_peak_bench(args)
+        return
     set_workload(args.workload)
     if WORKLOAD == BATCH_WORKLOAD:
         batch_bench(args)
@@ -552,6 +737,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     _native.load()  # the library must be built (fails loudly otherwise)
 
+    probe, probe_runs = fp64_peak(local)
+
     w, v, tau, X, sum_l, flops = workload_inputs(WORKLOAD)
     n, b, nev, cplx = w["n"], w["b"], w["nev"], w["complex_"]
     es = esize(w)
@@ -564,7 +751,8 @@ def main():
     info = plan.info()
 
     # parity pass on the pristine block (columns checked by the CPU baseline)
-    cols, Xs = cpu_sample(v, tau, X, w, args.cpu_cols)
+    ncpu = args.cpu_cols if args.cpu_cols else sample_cols(w, sum_l, 5e11)
+    cols, Xs = cpu_sample(v, tau, X, w, ncpu)
     plan.set_reflectors(dv, dt)
     plan.execute(q)
     P.stream_check()
@@ -617,15 +805,16 @@ def main():
             sp.execute(qs)
         torch.cuda.synchronize()
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        for _ in range(args.split_steps):
-            sp.set_reflectors(dv, dt)
-            sp.execute(qs)
-        s1.record(stream)
-        torch.cuda.synchronize()
+        with ClockSampler(local) as sclocks:
+            s0.record(stream)
+            for _ in range(args.split_steps):
+                sp.set_reflectors(dv, dt)
+                sp.execute(qs)
+            s1.record(stream)
+            torch.cuda.synchronize()
         P.stream_check()
         split_tc = {"ms_per_step": s0.elapsed_time(s1) / args.split_steps, "steps": args.split_steps,
-                    "cols": split_cols}
+                    "cols": split_cols, "clocks": sclocks.summary()}
         sp.close()
         del qs
 
@@ -676,19 +865,43 @@ def main():
     e2e = {"value": flops * args.e2e_steps * world / e2e_s / 1e12, "unit": "TFLOP/s",
            "h2d_bytes_per_step": int(v.nbytes + tau.nbytes + n * nev * es), "d2h_bytes_per_step": int(n * nev * es),
            "steps": args.e2e_steps, "api": api}
+    P.release_cache()
+    plan.close()
+    del hv, ht, hq, q, dv, dt
+
+    # the other configurations, each as a sub-object of the same line
+    extras = {}
+    names = []
+    if args.extras == "default":
+        names = list(EXTRA_WORKLOADS) if default_workload and not split else []
+    elif args.extras != "none":
+        names = [x for x in args.extras.split(",") if x]
+    if rank == 0:
+        for nm in names:
+            torch.cuda.empty_cache()
+            if nm == BATCH_WORKLOAD:
+                m = batch_measure(args.extra_steps)
+                m["of_fp64_peak"] = m["batched"]["tflops"] / peak_at_clock(probe, m["clocks"]["sm_mhz"])
+            else:
+                m = measure_fp64(nm, args.extra_steps, 0, parity_cols=8 if nm != "real-n512-b32-uniform" else 512)
+                m["of_fp64_peak"] = m["apply_tflops"] / peak_at_clock(probe, m["clocks"]["sm_mhz"])
+            extras[nm] = m
 
     if rank == 0:
         apply_avg = sum(apply_ms) / len(apply_ms)
         achieved = flops / (apply_avg * 1e-3) / 1e12
         cs = clocks.summary()
-        peak_at_clock = None
-        if cs["sm_mhz"]:
-            peak_at_clock = SMS * DFMA_PER_CLK_SM * 2 * cs["sm_mhz"] * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None if split else recorded_traffic(),
-                "kernel": "tbbt::apply_kernel<zdouble, 0>" if cplx else f"tbbt::apply_kernel<double, {b if b in (32, 64) else 0}>",
-                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe; DFMA probe 1.198 TF)",
-                "peak_at_sampled_clock": peak_at_clock,
+        peak = peak_at_clock(probe, cs["sm_mhz"])
+        derived_at_clock = SMS * DFMA_PER_CLK_SM * 2 * cs["sm_mhz"] * 1e6 / 1e12 if cs["sm_mhz"] else None
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None if split else recorded_traffic(WORKLOAD),
+                "kernel": "tbbt::apply_kernel<zdouble, -1>" if cplx else f"tbbt::apply_kernel<double, {b if b in (32, 64) else 0}>",
+                "peak_source": f"measured: library FP64 probe ({probe['kind']}, {probe['tflops']:.4f} TFLOP/s at "
+                               f"{probe['sm_mhz']} MHz) scaled to the {cs['sm_mhz']} MHz sampled during the timed steps",
+                "fp64_probe": probe_runs,
+                "peak_derived": derived_at_clock,
+                "frac_of_derived": achieved / derived_at_clock if derived_at_clock else None,
+                "peak_derived_source": "152 SMs x 2 DFMA/clk x 2 flop x sampled SM clock",
                 "algorithmic_bytes_per_launch": int(2 * n * nev * es + sum_l * es)}
         Zo, cpu_s, cores = run_oracle_sample(v, tau, w, Xs)
         cpu = {"value": (16 if cplx else 4) * len(cols) * sum_l / cpu_s / 1e12, "unit": "TFLOP/s", "cores": cores,
@@ -710,6 +923,7 @@ def main():
             "vs_baseline": None, "dtype": dtype_name(w), "data": "synthetic", "config": config_dict(w),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": LAUNCHES_PER_STEP[args.variant] * args.steps,
             "clocks": cs, "relayout_ms_avg": sum(relayout_ms) / len(relayout_ms), "apply_ms_avg": apply_avg,
+            "of_fp64_peak": value / peak if not split else None,
             "launch": info, "variant": {"fp64": "fp64", "split": "split_bf16", "split-tc": "split_bf16_tc"}[args.variant],
         }
         if fp64_cmp:
@@ -723,10 +937,11 @@ def main():
                 "tensor_tflops": tc_tensor_flops(w) / (sms * 1e-3) / 1e12,
                 "tensor_frac_of_bf16_peak": tc_tensor_flops(w) / (sms * 1e-3) / 1e12 / BF16_PEAK_TFLOPS,
                 "max_abs_err_vs_oracle": float(np.abs(Zo - split_tc["cols"]).max()),
-                "err_sample": cpu["sample"],
+                "err_sample": cpu["sample"], "clocks": split_tc["clocks"],
             }
+        if extras:
+            line["configs"] = extras
         print(json.dumps(line), flush=True)
-    plan.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -320,6 +320,22 @@ tbbt_status tbbt_trans_ev_band_to_full_d(const double *a, int64_t lda, const dou
 tbbt_status tbbt_trans_ev_band_to_full_z(const void *a, int64_t lda, const void *tau, int64_t n, int64_t nbw,
                                          int64_t nev, void *q, int64_t ldq, void *stream);
 
+/* -------------------------------------------------------------------------
+ * FP64 rate probe (a measurement aid; the paper has no counterpart). The
+ * FP64 back-transformation is bound by the FP64 pipe, so its roofline
+ * denominator is that pipe's rate, measured on the device in use:
+ * kind 0 launches `blocks` x `threads` threads that each run 8 independent
+ * FP64 FMA chains for `iters` iterations; kind 1 runs, per warp, 4
+ * independent FP64 tensor-core products (mma.sync m8n8k4) for `iters`
+ * iterations. *flops receives the launch's flop count (2 per FMA, 512 per
+ * m8n8k4 product); time the launch with events on `stream`.
+ * d_sink: device array of blocks * threads doubles (written, meaningless).
+ * Errors: TBBT_EINVAL (kind, threads not a multiple of 32 in [32, 1024],
+ * blocks < 1, iters < 1, null pointers), TBBT_ECUDA.
+ * ------------------------------------------------------------------------- */
+tbbt_status tbbt_fp64_probe(int32_t kind, int32_t blocks, int32_t threads, int64_t iters, double *d_sink,
+                            double *flops, void *stream);
+
 /* Host-side check of the block schedule (no GPU needed): largest number of
  * rows a thread block ever holds at once for these parameters, or -1 if the
  * schedule would touch a row twice in one step. Used by tests to show the

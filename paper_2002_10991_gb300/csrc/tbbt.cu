@@ -20,6 +20,7 @@
 #include "tc_split.cuh"
 #include "bulge.cuh"
 #include "b2f.cuh"
+#include "probe.cuh"
 
 using tbbt::StoreGeom;
 using tbbt::zdouble;
@@ -1128,3 +1129,23 @@ tbbt_status tbbt_bulge_chase_z(const void *band, int64_t ldb, int64_t n, int64_t
 }
 }  // extern "C"
 
+
+// ---------------------------------------------------------------------------
+// FP64 rate probes (the FP64 roofline's denominators, measured)
+// ---------------------------------------------------------------------------
+extern "C" tbbt_status tbbt_fp64_probe(int32_t kind, int32_t blocks, int32_t threads, int64_t iters, double *d_sink,
+                                       double *flops, void *stream) {
+  if (kind != 0 && kind != 1) return TBBT_EINVAL;
+  if (blocks < 1 || threads < 32 || threads > 1024 || threads % 32 || iters < 1 || !d_sink || !flops)
+    return TBBT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (kind == 0) {
+    tbbt::probe::fma_probe_kernel<<<blocks, threads, 0, s>>>(d_sink, iters, 0.999999, 1e-6);
+    *flops = 2.0 * tbbt::probe::kChains * (double)iters * (double)blocks * threads;
+  } else {
+    tbbt::probe::mma_probe_kernel<<<blocks, threads, 0, s>>>(d_sink, iters, 0.5);
+    *flops = 512.0 * tbbt::probe::kMmaAcc * (double)iters * (double)blocks * (threads / 32);
+  }
+  TBBT_CUDA_TRY(cudaGetLastError());
+  return TBBT_OK;
+}

@@ -26,6 +26,7 @@ shape ``(b+1, n)``; entries with ``c + d >= n`` are zero.
 from __future__ import annotations
 
 import math
+import os
 
 import numpy as np
 
@@ -58,19 +59,48 @@ def splitmix64(seed: int, stream: int, count: int, offset: int = 0) -> np.ndarra
         return _mix(key + idx * PHI)
 
 
+# Arrays longer than this are drawn in chunks on several host threads (the
+# draws are counter-based, so the result does not depend on the chunking).
+_CHUNK = 1 << 21
+
+
+def _chunked(n: int, fill) -> np.ndarray:
+    """out[a:b] = fill(a, b) over chunks of the index range, in parallel."""
+    out = np.empty(n, dtype=np.float64)
+    if n <= _CHUNK:
+        out[:] = fill(0, n)
+        return out
+    from concurrent.futures import ThreadPoolExecutor
+
+    def work(a):
+        b = min(a + _CHUNK, n)
+        out[a:b] = fill(a, b)
+
+    with ThreadPoolExecutor(max_workers=min(os.cpu_count() or 1, 32)) as ex:
+        list(ex.map(work, range(0, n, _CHUNK)))
+    return out
+
+
 def uniform(seed: int, stream: int, shape, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
     n = int(np.prod(shape)) if len(shape) else 1
-    u = (splitmix64(seed, stream, n) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
-    return (lo + (hi - lo) * u).reshape(shape)
+
+    def fill(a, b):
+        u = (splitmix64(seed, stream, b - a, a) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+        return lo + (hi - lo) * u
+
+    return _chunked(n, fill).reshape(shape)
 
 
 def normal(seed: int, stream: int, shape) -> np.ndarray:
     n = int(np.prod(shape)) if len(shape) else 1
-    w = splitmix64(seed, stream, 2 * n)
-    u1 = (w[0::2] >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
-    u2 = (w[1::2] >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
-    z = np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * math.pi * u2)
-    return z.reshape(shape)
+
+    def fill(a, b):
+        w = splitmix64(seed, stream, 2 * (b - a), 2 * a)
+        u1 = (w[0::2] >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+        u2 = (w[1::2] >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+        return np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * math.pi * u2)
+
+    return _chunked(n, fill).reshape(shape)
 
 
 # ----------------------------------------------------------------------------
@@ -154,15 +184,15 @@ def store_lengths(n: int, b: int, complex_: bool) -> np.ndarray:
     """Lengths L_k of the reflectors in generation order (the canonical store
     format: stage i = 0..n-3, sweep j = 0..ceil((n-i-2)/b)-1, L = min(b, n-r)
     with r = i+1+j*b; a Hermitian store ends with one length-1 reflector)."""
-    out = []
-    for i in range(0, max(n - 2, 0)):
-        s = -(-(n - i - 2) // b)
-        for j in range(s):
-            r = i + 1 + j * b
-            out.append(min(b, n - r))
+    i = np.arange(max(n - 2, 0), dtype=np.int64)
+    s = -(-(n - i - 2) // b)  # sweeps of stage i
+    stage = np.repeat(i, s)
+    first = np.repeat(np.cumsum(s) - s, s)  # index of reflector (i, 0)
+    j = np.arange(stage.size, dtype=np.int64) - first
+    L = np.minimum(b, n - (stage + 1 + j * b))
     if complex_ and n >= 2:
-        out.append(1)
-    return np.asarray(out, dtype=np.int64)
+        L = np.append(L, 1)
+    return L.astype(np.int64)
 
 
 def synthetic_store(n: int, b: int, seed: int, complex_: bool = False):
@@ -183,11 +213,14 @@ def synthetic_store(n: int, b: int, seed: int, complex_: bool = False):
     V = normal(seed, 21, (K, b)) / math.sqrt(max(b, 1))
     if complex_:
         V = V + 1j * (normal(seed, 22, (K, b)) / math.sqrt(max(b, 1)))
-    V = V.astype(dt)
+    V = V.astype(dt, copy=False)
+    short = np.nonzero(L < b)[0]  # only the last sweeps of a stage are truncated
     cols = np.arange(b)[None, :]
-    V[cols >= L[:, None]] = 0.0
+    V[short] = np.where(cols >= L[short][:, None], 0.0, V[short])
     V[:, 0] = 1.0
-    nrm2 = np.sum(np.abs(V) ** 2, axis=1)
+    nrm2 = np.einsum("kj,kj->k", V.real, V.real)
+    if complex_:
+        nrm2 = nrm2 + np.einsum("kj,kj->k", V.imag, V.imag)
     if complex_:
         theta = uniform(seed, 23, (K,), 0.0, 2.0 * math.pi)
         tau = (1.0 - np.exp(1j * theta)) / nrm2
