@@ -663,6 +663,134 @@ def measure_fp64(name: str, steps: int, warmup: int, parity_cols: int = 8):
             f"tbbt::apply_kernel<double, {b if b in (32, 64) else 0}>"}
 
 
+def band_times(W: np.ndarray, Z):
+    """B Z for the Hermitian band matrix B in lower band storage W (b+1, n),
+    on the device, with Z (n x m) a device tensor: one shifted product per
+    diagonal (B is never formed)."""
+    import torch
+
+    b = W.shape[0] - 1
+    Wd = torch.from_numpy(W).to(Z.device)
+    out = Wd[0].real.to(Z.dtype)[:, None] * Z
+    for k in range(1, b + 1):
+        c = Wd[k, : Z.shape[0] - k][:, None].to(Z.dtype)
+        out[k:] += c * Z[:-k]
+        out[:-k] += c.conj() * Z[k:]
+    return out
+
+
+def eigen_quality(W: np.ndarray, w, Z, sample: int = 1024, seed: int = 5):
+    """Residual max_j ||B z_j - w_j z_j|| / ||B||_2 over all columns, the
+    largest deviation of a column norm from 1, and max |z_i^H z_j - delta_ij|
+    for a seeded sample of columns against all columns (the whole Z^H Z when
+    nev <= sample). ||B||_2 is taken as max_j |w_j| over the computed
+    eigenvalues, a lower bound (so the reported residual is an upper bound)."""
+    import torch
+
+    nev = Z.shape[1]
+    R = band_times(W, Z) - Z * w[None, :]
+    bn = max(w.abs().max().item(), np.finfo(float).tiny)
+    res = torch.linalg.vector_norm(R, dim=0).max().item() / bn
+    del R
+    norms = torch.linalg.vector_norm(Z, dim=0)
+    if nev <= sample:
+        cols = torch.arange(nev, device=Z.device)
+    else:
+        g = torch.Generator(device="cpu").manual_seed(seed)
+        cols = torch.randperm(nev, generator=g)[:sample].sort().values.to(Z.device)
+    G = Z[:, cols].conj().t() @ Z
+    G[torch.arange(len(cols), device=Z.device), cols] -= 1.0
+    return {"residual_max_over_norm": res, "norm": "max |computed eigenvalue| (<= ||B||_2)",
+            "max_abs_column_norm_minus_1": (norms - 1.0).abs().max().item(),
+            "orthogonality_max": G.abs().max().item(),
+            "orthogonality_columns": f"{len(cols)} sampled of {nev} against all" if nev > sample else "all"}
+
+
+def split_accuracy(name: str):
+    """The split-precision form on true eigenvectors at the workload's size:
+    GPU bulge chase of the workload's band (Eq. 6b), GPU tridiagonal
+    eigensolver (Eq. 6c), then the tcgen05 split-precision back-transform
+    (Eq. 6d); residual and orthogonality of the band matrix's eigenpairs."""
+    import torch
+
+    import paper_2002_10991_gb300 as P
+
+    w_ = I.WORKLOADS[name]
+    n, b, nev = w_["n"], w_["b"], w_["nev"]
+    W = I.band_for(name)
+    band = torch.from_numpy(np.ascontiguousarray(W.T)).cuda().t()
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record(stream)
+    v, tau, d, e = P.bulge_chase(band)
+    ev[1].record(stream)
+    w, X = P.tridiag_eig(d, e, nev)
+    ev[2].record(stream)
+    sp = P.Plan(False, n, b, nev, variant=VARIANTS["split-tc"])
+    sp.set_reflectors(v, tau)
+    sp.execute(X)
+    ev[3].record(stream)
+    P.stream_check()
+    sp.close()
+    del band, v, tau
+    q = eigen_quality(W, w, X)
+    q.update({"chain": "GPU bulge chase -> GPU tridiagonal eigensolver -> split-tc back-transform",
+              "workload_band": name, "n": n, "nbw": b, "nev": nev,
+              "ms": {"bulge_chase": ev[0].elapsed_time(ev[1]), "tridiag_eig": ev[1].elapsed_time(ev[2]),
+                     "split_back_transform": ev[2].elapsed_time(ev[3])}})
+    return q
+
+
+def chain_n512():
+    """The plain method on the n = 512 uniform band, all 512 eigenvectors:
+    bulge chase, tridiagonal eigensolver and back-transform on the GPU
+    against the oracle's bulge chase, implicit QL and back-transform on the
+    host (eigenvalues, eigenvectors up to sign, residual, orthogonality)."""
+    import torch
+
+    import oracle
+    import paper_2002_10991_gb300 as P
+
+    name = "real-n512-b32-uniform"
+    w_ = I.WORKLOADS[name]
+    n, b, nev = w_["n"], w_["b"], w_["nev"]
+    W = I.band_for(name)
+    band = torch.from_numpy(np.ascontiguousarray(W.T)).cuda().t()
+    stream = torch.cuda.current_stream()
+
+    def gpu_chain():
+        v, tau, d, e = P.bulge_chase(band)
+        w, X = P.tridiag_eig(d, e, nev)
+        P.trans_ev_tridi_to_band(v, tau, n, b, nev, X)
+        return w, X
+
+    for _ in range(2):
+        gpu_chain()
+    torch.cuda.synchronize()
+    steps = 5
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        w, X = gpu_chain()
+    e1.record(stream)
+    P.stream_check()
+    ms = e0.elapsed_time(e1) / steps
+    t0 = time.perf_counter()
+    v_o, t_o, d_o, e_o = oracle.bulge_chase(W)
+    lam_o, Xo = oracle.tridiag_ql(d_o, e_o)
+    Zo = oracle.back_transform(v_o, t_o, n, b, np.asfortranarray(Xo[:, :nev]), nthreads=1)
+    cpu_ms = (time.perf_counter() - t0) * 1e3
+    Zg, wg = X.cpu().numpy(), w.cpu().numpy()
+    sgn = np.sign(np.sum(Zg * Zo, axis=0))
+    q = eigen_quality(W, w, X)
+    q.update({"workload": name, "n": n, "nbw": b, "nev": nev, "steps": steps, "ms_per_chain": ms,
+              "chain": "GPU bulge chase -> GPU tridiagonal eigensolver -> GPU back-transform",
+              "oracle_chain_ms": cpu_ms, "oracle_chain_cores": 1,
+              "max_abs_eigenvalue_err_vs_oracle": float(np.abs(wg - lam_o[:nev]).max()),
+              "max_abs_eigvec_err_vs_oracle_up_to_sign": float(np.abs(Zg - Zo * sgn[None, :]).max())})
+    return q
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -683,6 +811,9 @@ def main():
                          f"({', '.join(EXTRA_WORKLOADS)}); 'default' = all of them for the default workload, "
                          "'none' = skip")
     ap.add_argument("--extra-steps", type=int, default=2, help="timed steps of each extra configuration")
+    ap.add_argument("--split-accuracy", type=int, default=1,
+                    help="1: residual and orthogonality of the split form on true eigenvectors of the "
+                         "workload's band (GPU bulge chase and tridiagonal eigensolver first)")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="named workload (default: the benchmark workload; others are for profiler captures, "
                          "the batched-form measurement, the FP64 probe sweep (fp64-peak), the GPU bulge chase (" +
@@ -817,6 +948,10 @@ def main():
                     "cols": split_cols, "clocks": sclocks.summary()}
         sp.close()
         del qs
+        if args.split_accuracy and w["kind"] == "dft":
+            torch.cuda.empty_cache()
+            split_tc["accuracy"] = split_accuracy(WORKLOAD)
+            torch.cuda.empty_cache()
 
     fp64_cmp = None
     if split:
@@ -882,8 +1017,12 @@ def main():
             if nm == BATCH_WORKLOAD:
                 m = batch_measure(args.extra_steps)
                 m["of_fp64_peak"] = m["batched"]["tflops"] / peak_at_clock(probe, m["clocks"]["sm_mhz"])
+            elif nm == "real-n512-b32-uniform":
+                m = measure_fp64(nm, max(args.extra_steps, 5), 2, parity_cols=512)
+                m["of_fp64_peak"] = m["apply_tflops"] / peak_at_clock(probe, m["clocks"]["sm_mhz"])
+                m["gpu_chain"] = chain_n512()
             else:
-                m = measure_fp64(nm, args.extra_steps, 0, parity_cols=8 if nm != "real-n512-b32-uniform" else 512)
+                m = measure_fp64(nm, args.extra_steps, 0, parity_cols=8)
                 m["of_fp64_peak"] = m["apply_tflops"] / peak_at_clock(probe, m["clocks"]["sm_mhz"])
             extras[nm] = m
 
@@ -939,6 +1078,8 @@ def main():
                 "max_abs_err_vs_oracle": float(np.abs(Zo - split_tc["cols"]).max()),
                 "err_sample": cpu["sample"], "clocks": split_tc["clocks"],
             }
+            if "accuracy" in split_tc:
+                line["split_tc"]["accuracy_true_eigenvectors"] = split_tc["accuracy"]
         if extras:
             line["configs"] = extras
         print(json.dumps(line), flush=True)

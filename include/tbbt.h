@@ -295,6 +295,35 @@ tbbt_status tbbt_bulge_chase_z(const void *band, int64_t ldb, int64_t n, int64_t
                                double *d, double *e, void *stream);
 
 /* -------------------------------------------------------------------------
+ * Tridiagonal eigensolver for the nev lowest eigenpairs (Eq. 6c; Sec. 2.1:
+ * only the wanted eigenvectors of the tridiagonal matrix are computed), the
+ * step whose eigenvectors X the back-transformation Eq. 6d takes. T is the
+ * real symmetric tridiagonal matrix with diagonal d[0..n-1] and
+ * sub-diagonal e[0..n-2] (the d, e of tbbt_bulge_chase_*).
+ *
+ * Eigenvalues by multisection on Sturm counts, eigenvectors by inverse
+ * iteration with a pivoted tridiagonal LU (three solves from a
+ * pseudo-random start), then modified Gram-Schmidt inside every cluster of
+ * eigenvalues chained by gaps below 1e-4 ||T||. All in FP64.
+ *
+ * d, e:  device, n and n-1 doubles; read only.
+ * w:     device output, nev doubles: the nev smallest eigenvalues, ascending.
+ * x:     device output, n x nev column-major, ldx >= max(1, n): the
+ *        orthonormal eigenvectors (column k belongs to w[k]; its entry of
+ *        largest magnitude is positive, unless re-orthogonalisation in a
+ *        cluster changed it). xtype TBBT_REAL64: doubles; TBBT_COMPLEX128:
+ *        interleaved complex doubles with zero imaginary parts (the X of a
+ *        Hermitian problem). Rows n..ldx-1 are not written.
+ * Runs on `stream` without host synchronisation; allocates and frees about
+ * 5.1 * n * nev * 8 bytes of workspace stream-ordered (13 GB at n = 32768,
+ * nev = 9830). The cost of a cluster of m eigenvalues grows as m^2 n.
+ * Errors: TBBT_EINVAL (n < 0, nev outside [0, n], ldx < max(1, n), xtype,
+ * null or misaligned pointers when there is work), TBBT_ENOMEM, TBBT_ECUDA.
+ * ------------------------------------------------------------------------- */
+tbbt_status tbbt_tridiag_eig(const double *d, const double *e, int64_t n, int64_t nev, double *w, void *x,
+                             int64_t ldx, tbbt_dtype xtype, void *stream);
+
+/* -------------------------------------------------------------------------
  * Band -> full back-transformation of eigenvectors (Eq. 6e, Sec. 2.1):
  * C = P^* Y = Q1 Y, Q1 = H_0 H_1 ... H_{K1-1}, K1 = max(n - nbw, 0), the
  * reflectors of the full -> band reduction (Eq. 6a). Reflector c acts on rows

@@ -16,4 +16,5 @@ from .api import (  # noqa: F401
     trans_ev_tridi_to_band,
     trans_ev_tridi_to_band_host,
     trans_ev_tridi_to_band_noalloc,
+    tridiag_eig,
 )

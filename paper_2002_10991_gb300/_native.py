@@ -100,6 +100,8 @@ def load():
             f = getattr(L, name)
             f.restype = c_int
             f.argtypes = [p, i64, p, i64, i64, i64, p, i64, p]
+        L.tbbt_tridiag_eig.restype = c_int
+        L.tbbt_tridiag_eig.argtypes = [p, p, i64, i64, p, p, i64, c_int, p]
         L.tbbt_fp64_probe.restype = c_int
         L.tbbt_fp64_probe.argtypes = [i32, i32, i32, i64, p, ctypes.POINTER(ctypes.c_double), p]
         L.tbbt_schedule_max_live_rows.restype = i64

@@ -183,6 +183,35 @@ def bulge_chase(band, nbw: int | None = None, stream=None):
     return hh_v, hh_tau, d, e
 
 
+def tridiag_eig(d, e, nev: int, complex_out: bool = False, x=None, stream=None):
+    """Eq. 6c on the GPU: the nev smallest eigenvalues (ascending) and their
+    orthonormal eigenvectors of the symmetric tridiagonal matrix with
+    diagonal ``d`` (n,) and sub-diagonal ``e`` (n-1,), float64 CUDA tensors.
+    Returns (w (nev,), X (n x nev, column-major)); X is complex128 with zero
+    imaginary parts when ``complex_out`` (the X of a Hermitian problem), or
+    written into ``x`` if given (column-major, ldx >= n)."""
+    import torch
+
+    n = int(d.numel())
+    if nev < 0 or nev > n:
+        raise ValueError(f"nev={nev} outside [0, {n}]")
+    _need_flat(d, "d", torch.float64, n)
+    _need_flat(e, "e", torch.float64, max(n - 1, 0))
+    dt = torch.complex128 if complex_out else torch.float64
+    w = torch.empty(nev, dtype=torch.float64, device=d.device)
+    if x is None:
+        x = torch.empty((nev, n), dtype=dt, device=d.device).t()
+    else:
+        _check_q(x, n, nev, dt)
+    ldx = _resolve_ldq(x, n, nev, None)
+    st = _native.load().tbbt_tridiag_eig(
+        ctypes.c_void_p(d.data_ptr() if n else 0), ctypes.c_void_p(e.data_ptr() if n > 1 else 0), n, nev,
+        ctypes.c_void_p(w.data_ptr() if nev else 0), ctypes.c_void_p(x.data_ptr() if x.numel() else 0), ldx,
+        COMPLEX128 if complex_out else REAL64, _stream_handle(stream))
+    _check(st, "tbbt_tridiag_eig")
+    return w, x
+
+
 def trans_ev_band_to_full(a, tau, n: int, nbw: int, nev: int, q, stream=None):
     """Eq. 6e on device tensors: q[:n, :nev] <- H_0 ... H_{n-nbw-1} q[:n, :nev]
     with the full -> band reflectors held LAPACK-style below the band of

@@ -21,6 +21,7 @@
 #include "bulge.cuh"
 #include "b2f.cuh"
 #include "probe.cuh"
+#include "tridiag.cuh"
 
 using tbbt::StoreGeom;
 using tbbt::zdouble;
@@ -1148,4 +1149,98 @@ extern "C" tbbt_status tbbt_fp64_probe(int32_t kind, int32_t blocks, int32_t thr
   }
   TBBT_CUDA_TRY(cudaGetLastError());
   return TBBT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Tridiagonal eigensolver for the nev lowest eigenpairs (Eq. 6c)
+// ---------------------------------------------------------------------------
+namespace {
+// Threads per eigenvalue in the multisection: the fewest (least FP64 work)
+// that still give every SM sub-partition about one warp.
+int32_t bisect_group(int64_t nev, int sms) {
+  const int64_t want = (int64_t)std::max(sms, 1) * 4 * 32 * 8 / 10;
+  int32_t P = 1;
+  while (P < 32 && nev * P < want) P *= 2;
+  return P;
+}
+
+tbbt_status tridiag_eig_impl(const double *d, const double *e, int64_t n, int64_t nev, double *w, void *x,
+                             int64_t ldx, tbbt_dtype xt, cudaStream_t s) {
+  namespace te = tbbt::te;
+  if (n < 0 || n > ((int64_t)1 << 30) || nev < 0 || nev > n) return TBBT_EINVAL;
+  if (xt != TBBT_REAL64 && xt != TBBT_COMPLEX128) return TBBT_EINVAL;
+  if (ldx < std::max<int64_t>(1, n)) return TBBT_EINVAL;
+  if (n == 0 || nev == 0) return TBBT_OK;
+  if (!d || !w || !x || (n > 1 && !e)) return TBBT_EINVAL;
+  const size_t xs = xt == TBBT_COMPLEX128 ? 16 : 8;
+  if (((uintptr_t)d | (uintptr_t)w | (uintptr_t)(n > 1 ? e : d)) % 8 || (uintptr_t)x % xs) return TBBT_EINVAL;
+  const size_t nn = (size_t)n * (size_t)nev;
+  int dev = 0, sms = 0;
+  TBBT_CUDA_TRY(cudaGetDevice(&dev));
+  TBBT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  // workspace: e^2, bounds, five [row][vector] arrays, pivots, and a real
+  // column-major copy of X when the output is complex
+  const size_t b_e2 = round256(sizeof(double) * (size_t)std::max<int64_t>(n, 1));
+  const size_t b_bounds = round256(sizeof(te::Bounds));
+  const size_t b_arr = round256(sizeof(double) * nn);
+  const size_t b_piv = round256(nn);
+  const size_t b_xr = xt == TBBT_COMPLEX128 ? b_arr : 0;
+  const size_t total = b_e2 + b_bounds + 5 * b_arr + b_piv + b_xr;
+  unsigned char *ws = nullptr;
+  TBBT_CUDA_TRY(cudaMallocAsync((void **)&ws, total, s));
+  tbbt_status rs = TBBT_OK;
+  do {
+    double *e2 = (double *)ws;
+    te::Bounds *bounds = (te::Bounds *)(ws + b_e2);
+    unsigned char *p = ws + b_e2 + b_bounds;
+    te::InvitArgs A;
+    A.d = d;
+    A.e = e;
+    A.n = (int32_t)n;
+    A.nev = (int32_t)nev;
+    A.w = w;
+    A.bounds = bounds;
+    A.u0 = (double *)p;
+    A.u1 = (double *)(p + b_arr);
+    A.u2 = (double *)(p + 2 * b_arr);
+    A.lm = (double *)(p + 3 * b_arr);
+    A.y = (double *)(p + 4 * b_arr);
+    A.piv = p + 5 * b_arr;
+    double *xr = xt == TBBT_COMPLEX128 ? (double *)(p + 5 * b_arr + b_piv) : (double *)x;
+    const int64_t ldr = xt == TBBT_COMPLEX128 ? n : ldx;
+    te::te_bounds_kernel<<<1, te::BOUNDS_THREADS, 0, s>>>(d, n > 1 ? e : d, (int32_t)n, e2, bounds);
+    if (cudaGetLastError() != cudaSuccess) { rs = TBBT_ECUDA; break; }
+    const int32_t P = bisect_group(nev, sms);
+    const int64_t bthreads = 128;
+    const unsigned bblocks = (unsigned)((nev * P + bthreads - 1) / bthreads);
+    switch (P) {
+      case 1: te::te_bisect_kernel<1><<<bblocks, bthreads, 0, s>>>(d, e2, (int32_t)n, (int32_t)nev, bounds, w); break;
+      case 2: te::te_bisect_kernel<2><<<bblocks, bthreads, 0, s>>>(d, e2, (int32_t)n, (int32_t)nev, bounds, w); break;
+      case 4: te::te_bisect_kernel<4><<<bblocks, bthreads, 0, s>>>(d, e2, (int32_t)n, (int32_t)nev, bounds, w); break;
+      case 8: te::te_bisect_kernel<8><<<bblocks, bthreads, 0, s>>>(d, e2, (int32_t)n, (int32_t)nev, bounds, w); break;
+      case 16: te::te_bisect_kernel<16><<<bblocks, bthreads, 0, s>>>(d, e2, (int32_t)n, (int32_t)nev, bounds, w); break;
+      default: te::te_bisect_kernel<32><<<bblocks, bthreads, 0, s>>>(d, e2, (int32_t)n, (int32_t)nev, bounds, w); break;
+    }
+    if (cudaGetLastError() != cudaSuccess) { rs = TBBT_ECUDA; break; }
+    te::te_invit_kernel<<<(unsigned)((nev + te::INVIT_THREADS - 1) / te::INVIT_THREADS), te::INVIT_THREADS, 0, s>>>(A);
+    if (cudaGetLastError() != cudaSuccess) { rs = TBBT_ECUDA; break; }
+    dim3 tg((unsigned)((n + 31) / 32), (unsigned)((nev + 31) / 32));
+    te::te_transpose_kernel<<<tg, dim3(32, 8), 0, s>>>(A.y, (int32_t)n, (int32_t)nev, xr, ldr);
+    if (cudaGetLastError() != cudaSuccess) { rs = TBBT_ECUDA; break; }
+    te::te_reorth_kernel<<<(unsigned)nev, te::REORTH_THREADS, 0, s>>>(w, (int32_t)n, (int32_t)nev, bounds, xr, ldr);
+    if (cudaGetLastError() != cudaSuccess) { rs = TBBT_ECUDA; break; }
+    if (xt == TBBT_COMPLEX128) {
+      te::te_to_complex_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(xr, ldr, (int32_t)n, (int32_t)nev,
+                                                                        (double2 *)x, ldx);
+      if (cudaGetLastError() != cudaSuccess) { rs = TBBT_ECUDA; break; }
+    }
+  } while (0);
+  cudaFreeAsync(ws, s);
+  return rs;
+}
+}  // namespace
+
+extern "C" tbbt_status tbbt_tridiag_eig(const double *d, const double *e, int64_t n, int64_t nev, double *w,
+                                        void *x, int64_t ldx, tbbt_dtype xtype, void *stream) {
+  return tridiag_eig_impl(d, e, n, nev, w, x, ldx, xtype, (cudaStream_t)stream);
 }

@@ -1,0 +1,343 @@
+// Tridiagonal eigensolver for the nev lowest eigenpairs (Eq. 6c): the step
+// between the bulge chase (Eq. 6b) and the back-transformation (Eq. 6d).
+// ELPA computes only the wanted eigenvectors of the tridiagonal matrix
+// (Sec. 2.1); here that is done with O(n * nev) work, the form that suits a
+// GPU whose FP64 units are its scarce resource:
+//
+//  1. te_bounds_kernel: Gershgorin interval, ||T|| and e_i^2 (one block).
+//  2. te_bisect_kernel: eigenvalue k by bisection on Sturm counts (the
+//     number of negative pivots of the LDL^T factorisation of T - sigma I is
+//     the number of eigenvalues below sigma). P threads share one eigenvalue
+//     and evaluate P points of its bracket per round (multisection), so a
+//     round shrinks the bracket (P + 1)-fold.
+//  3. te_invit_kernel: eigenvector k by inverse iteration, one thread per
+//     vector: Gaussian elimination with partial pivoting of T - lambda_k I
+//     (the factor U has two super-diagonals), then solves from a
+//     pseudo-random start, normalised after each. Factors and iterates are
+//     stored [row][vector], so each step of the recurrences is one coalesced
+//     access across the vectors of a warp.
+//  4. te_transpose_kernel: [row][vector] -> column-major X.
+//  5. te_reorth_kernel: modified Gram-Schmidt (twice) inside each cluster of
+//     eigenvalues closer than a fixed fraction of ||T||; a block per cluster.
+//     Inverse iteration leaves vectors of well-separated eigenvalues
+//     orthogonal to about eps ||T|| / gap; the clusters are where that bound
+//     is loose.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <float.h>
+#include <stdint.h>
+
+namespace tbbt {
+namespace te {
+
+constexpr int BOUNDS_THREADS = 256;
+constexpr int INVIT_THREADS = 128;
+constexpr int REORTH_THREADS = 256;
+// eigenvalues closer than this fraction of ||T|| (chained) form a cluster
+constexpr double CLUSTER_TOL = 1e-4;
+// solves of inverse iteration per vector
+constexpr int INVIT_STEPS = 3;
+
+struct Bounds {
+  double gl, gu;     // Gershgorin interval, widened
+  double tnorm;      // max(|gl|, |gu|)
+  double pivmin;     // smallest pivot magnitude allowed in a Sturm count
+  double pert;       // replacement of a vanishing pivot in inverse iteration
+};
+
+// Gershgorin bounds, e2 = e^2, the largest e^2 (one block of BOUNDS_THREADS).
+__global__ void te_bounds_kernel(const double *__restrict__ d, const double *__restrict__ e, int32_t n,
+                                 double *__restrict__ e2, Bounds *out) {
+  __shared__ double s_lo[BOUNDS_THREADS], s_hi[BOUNDS_THREADS], s_e2[BOUNDS_THREADS];
+  double lo = DBL_MAX, hi = -DBL_MAX, me2 = 0.0;
+  for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double em = i > 0 ? fabs(e[i - 1]) : 0.0;
+    const double ep = i + 1 < n ? fabs(e[i]) : 0.0;
+    lo = fmin(lo, d[i] - em - ep);
+    hi = fmax(hi, d[i] + em + ep);
+    if (i + 1 < n) {
+      const double s = e[i] * e[i];
+      e2[i] = s;
+      me2 = fmax(me2, s);
+    }
+  }
+  s_lo[threadIdx.x] = lo;
+  s_hi[threadIdx.x] = hi;
+  s_e2[threadIdx.x] = me2;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      s_lo[threadIdx.x] = fmin(s_lo[threadIdx.x], s_lo[threadIdx.x + w]);
+      s_hi[threadIdx.x] = fmax(s_hi[threadIdx.x], s_hi[threadIdx.x + w]);
+      s_e2[threadIdx.x] = fmax(s_e2[threadIdx.x], s_e2[threadIdx.x + w]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    Bounds b;
+    const double eps = DBL_EPSILON;
+    b.tnorm = fmax(fabs(s_lo[0]), fabs(s_hi[0]));
+    b.pivmin = DBL_MIN * fmax(1.0, s_e2[0]);
+    const double pad = 2.0 * eps * b.tnorm * (double)n + 2.0 * b.pivmin;
+    b.gl = s_lo[0] - pad - DBL_MIN;
+    b.gu = s_hi[0] + pad + DBL_MIN;
+    b.pert = eps * fmax(b.tnorm, DBL_MIN);
+    *out = b;
+  }
+}
+
+// Number of eigenvalues of T below sigma: negative pivots of T - sigma I =
+// L D L^T, q_0 = d_0 - sigma, q_i = d_i - sigma - e_{i-1}^2 / q_{i-1}, a
+// pivot of magnitude below pivmin taken as -pivmin.
+__device__ __forceinline__ int32_t sturm_count(const double *__restrict__ d, const double *__restrict__ e2,
+                                               int32_t n, double sigma, double pivmin) {
+  int32_t cnt = 0;
+  double q = d[0] - sigma;
+  if (fabs(q) < pivmin) q = -pivmin;
+  cnt += q < 0.0;
+  for (int32_t i = 1; i < n; ++i) {
+    q = (d[i] - sigma) - e2[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    cnt += q < 0.0;
+  }
+  return cnt;
+}
+
+// Eigenvalue k (0-based, ascending) by multisection: the P threads of a
+// group (P divides 32; a warp holds whole groups) evaluate P interior points
+// of the bracket [lo, hi], count(lo) <= k < count(hi), and keep the
+// sub-interval between the last point of the leading run with count <= k
+// and the point after it (so the invariant holds even where rounding makes
+// the counts non-monotone). Stops when the bracket is within
+// 2 eps max(|lo|, |hi|) + eps ||T||, or cannot shrink.
+template <int P>
+__global__ void te_bisect_kernel(const double *__restrict__ d, const double *__restrict__ e2, int32_t n,
+                                 int32_t nev, const Bounds *__restrict__ bounds, double *__restrict__ w) {
+  static_assert(P >= 1 && P <= 32 && (32 % P) == 0, "group size must divide the warp");
+  const int32_t lane = threadIdx.x & 31;
+  const int32_t g = lane % P;     // index within the group
+  const int32_t base = lane - g;  // first lane of the group
+  const int32_t k = (int32_t)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / P);
+  const bool active = k < nev;
+  const Bounds B = *bounds;
+  const double eps = DBL_EPSILON;
+  const unsigned gbits = (P == 32) ? 0xffffffffu : ((1u << P) - 1u);
+  double lo = B.gl, hi = B.gu;
+  bool done = !active;  // uniform within a group: lo and hi are
+  for (int round = 0; round < 512; ++round) {
+    if (!done) done = hi - lo <= 2.0 * eps * fmax(fabs(lo), fabs(hi)) + eps * B.tnorm;
+    if (__all_sync(0xffffffffu, done)) break;
+    const double sigma = lo + (hi - lo) * ((double)(g + 1) / (double)(P + 1));
+    const bool below = done || sturm_count(d, e2, n, sigma, B.pivmin) <= k;
+    const unsigned grp = (__ballot_sync(0xffffffffu, below) >> base) & gbits;
+    // leading run of points with count <= k
+    const int32_t lead = (grp == gbits) ? P : __ffs(~grp) - 1;
+    const double s_lo = __shfl_sync(0xffffffffu, sigma, base + (lead > 0 ? lead - 1 : 0));
+    const double s_hi = __shfl_sync(0xffffffffu, sigma, base + (lead < P ? lead : P - 1));
+    if (!done) {
+      const double nlo = lead > 0 ? s_lo : lo;
+      const double nhi = lead < P ? s_hi : hi;
+      if (nlo == lo && nhi == hi) done = true;  // no representable progress
+      lo = nlo;
+      hi = nhi;
+    }
+  }
+  if (active && g == 0) w[k] = 0.5 * (lo + hi);
+}
+
+// splitmix64 finaliser, for the pseudo-random start vectors
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+struct InvitArgs {
+  const double *d, *e;
+  int32_t n, nev;
+  const double *w;
+  const Bounds *bounds;
+  // [row][vector] scratch, each n * nev: reciprocal of U's diagonal, U's
+  // first and second super-diagonal, multipliers, the iterate; pivots
+  // (1 = rows swapped)
+  double *u0, *u1, *u2, *lm, *y;
+  unsigned char *piv;
+};
+
+// Eigenvector k of T by inverse iteration (one thread per vector).
+__global__ void te_invit_kernel(InvitArgs A) {
+  const int32_t k = (int32_t)(blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+  if (k >= A.nev) return;
+  const int32_t n = A.n;
+  const size_t ld = (size_t)A.nev;
+  const double lam = A.w[k];
+  const double pert = A.bounds->pert;
+  auto at = [&](int32_t i) { return (size_t)i * ld + (size_t)k; };
+  // factor T - lam I = P L U with partial pivoting; a pivot below pert in
+  // magnitude (T - lam I is singular to working precision there) is
+  // replaced by +-pert
+  {
+    double a = A.d[0] - lam;
+    double b = n > 1 ? A.e[0] : 0.0;
+    for (int32_t i = 0; i + 1 < n; ++i) {
+      const double c = A.e[i];             // row i+1, column i
+      const double dn = A.d[i + 1] - lam;  // row i+1, column i+1
+      const double bn = i + 2 < n ? A.e[i + 1] : 0.0;
+      if (fabs(a) >= fabs(c)) {
+        if (fabs(a) < pert) a = a < 0.0 ? -pert : pert;
+        const double r = 1.0 / a;
+        const double m = c * r;
+        A.u0[at(i)] = r;
+        A.u1[at(i)] = b;
+        A.u2[at(i)] = 0.0;
+        A.lm[at(i)] = m;
+        A.piv[at(i)] = 0;
+        a = dn - m * b;
+        b = bn;
+      } else {
+        const double cp = fabs(c) < pert ? (c < 0.0 ? -pert : pert) : c;
+        const double r = 1.0 / cp;
+        const double m = a * r;
+        A.u0[at(i)] = r;
+        A.u1[at(i)] = dn;
+        A.u2[at(i)] = bn;
+        A.lm[at(i)] = m;
+        A.piv[at(i)] = 1;
+        a = b - m * dn;
+        b = -m * bn;
+      }
+    }
+    if (fabs(a) < pert) a = a < 0.0 ? -pert : pert;
+    A.u0[at(n - 1)] = 1.0 / a;
+    A.u1[at(n - 1)] = 0.0;
+    A.u2[at(n - 1)] = 0.0;
+  }
+  // pseudo-random start in [-1, 1)
+  const uint64_t key = mix64(0x2002109910ull ^ ((uint64_t)k * 0x9E3779B97F4A7C15ull));
+  for (int32_t i = 0; i < n; ++i) {
+    const uint64_t r = mix64(key + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull);
+    A.y[at(i)] = (double)(r >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+  }
+  for (int step = 0; step < INVIT_STEPS; ++step) {
+    // forward: apply the row interchanges and multipliers to y
+    double yk = A.y[at(0)];
+    for (int32_t i = 0; i + 1 < n; ++i) {
+      double yn = A.y[at(i + 1)];
+      const double m = A.lm[at(i)];
+      if (A.piv[at(i)]) {
+        const double t = yk;
+        yk = yn;
+        yn = t - m * yk;
+      } else {
+        yn = yn - m * yk;
+      }
+      A.y[at(i)] = yk;
+      yk = yn;
+    }
+    A.y[at(n - 1)] = yk;
+    // back substitution with U (diagonal, two super-diagonals), tracking the
+    // largest magnitude
+    double x1 = 0.0, x2 = 0.0, amax = 0.0;
+    for (int32_t i = n - 1; i >= 0; --i) {
+      const double x = (A.y[at(i)] - A.u1[at(i)] * x1 - A.u2[at(i)] * x2) * A.u0[at(i)];
+      A.y[at(i)] = x;
+      amax = fmax(amax, fabs(x));
+      x2 = x1;
+      x1 = x;
+    }
+    // normalise: scale by the largest entry first (no overflow in the sum)
+    const double s = amax > 0.0 ? 1.0 / amax : 1.0;
+    double ss = 0.0;
+    for (int32_t i = 0; i < n; ++i) {
+      const double v = A.y[at(i)] * s;
+      ss += v * v;
+    }
+    const double f = s / sqrt(ss);
+    // sign: the first entry of largest magnitude is positive
+    double best = 0.0, sgn = 1.0;
+    if (step == INVIT_STEPS - 1) {
+      for (int32_t i = 0; i < n; ++i) {
+        const double v = A.y[at(i)];
+        if (fabs(v) > best) {
+          best = fabs(v);
+          sgn = v < 0.0 ? -1.0 : 1.0;
+        }
+      }
+    }
+    for (int32_t i = 0; i < n; ++i) A.y[at(i)] *= f * sgn;
+  }
+}
+
+// [row][vector] (ld = nev) -> column-major x (ldx), 32 x 32 tiles.
+__global__ void te_transpose_kernel(const double *__restrict__ y, int32_t n, int32_t nev, double *__restrict__ x,
+                                    int64_t ldx) {
+  __shared__ double tile[32][33];
+  const int32_t i0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int32_t i = i0 + r, k = k0 + threadIdx.x;
+    if (i < n && k < nev) tile[r][threadIdx.x] = y[(size_t)i * nev + k];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int32_t k = k0 + r, i = i0 + threadIdx.x;
+    if (i < n && k < nev) x[(size_t)k * ldx + i] = tile[threadIdx.x][r];
+  }
+}
+
+__device__ __forceinline__ double block_sum(double v, double *red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int wid = threadIdx.x / 32, nw = blockDim.x / 32;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < nw; ++i) s += red[i];
+  return s;
+}
+
+// Modified Gram-Schmidt, twice, inside the cluster that starts at vector
+// blockIdx.x (vectors whose eigenvalues are chained by gaps below
+// CLUSTER_TOL * ||T||); blocks at no cluster start, or of one-vector
+// clusters, return at once.
+__global__ void te_reorth_kernel(const double *__restrict__ w, int32_t n, int32_t nev,
+                                 const Bounds *__restrict__ bounds, double *__restrict__ x, int64_t ldx) {
+  __shared__ double red[REORTH_THREADS / 32];
+  const int32_t j0 = blockIdx.x;
+  const double tol = CLUSTER_TOL * bounds->tnorm;
+  if (j0 > 0 && w[j0] - w[j0 - 1] < tol) return;  // not a cluster start
+  int32_t j1 = j0 + 1;
+  while (j1 < nev && w[j1] - w[j1 - 1] < tol) ++j1;
+  if (j1 - j0 < 2) return;
+  for (int32_t c = j0 + 1; c < j1; ++c) {
+    double *xc = x + (size_t)c * ldx;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int32_t p = j0; p < c; ++p) {
+        const double *xp = x + (size_t)p * ldx;
+        double s = 0.0;
+        for (int32_t i = threadIdx.x; i < n; i += blockDim.x) s += xp[i] * xc[i];
+        const double dot = block_sum(s, red);
+        for (int32_t i = threadIdx.x; i < n; i += blockDim.x) xc[i] -= dot * xp[i];
+        __syncthreads();
+      }
+    }
+    double s = 0.0;
+    for (int32_t i = threadIdx.x; i < n; i += blockDim.x) s += xc[i] * xc[i];
+    const double nrm = sqrt(block_sum(s, red));
+    const double f = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    for (int32_t i = threadIdx.x; i < n; i += blockDim.x) xc[i] *= f;
+    __syncthreads();
+  }
+}
+
+// Real column-major xr (ld ldr) -> complex x (ld ldx), imaginary parts 0.
+__global__ void te_to_complex_kernel(const double *__restrict__ xr, int64_t ldr, int32_t n, int32_t nev,
+                                     double2 *__restrict__ x, int64_t ldx) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * nev) return;
+  const int64_t k = t / n, i = t - k * n;
+  x[k * ldx + i] = make_double2(xr[k * ldr + i], 0.0);
+}
+
+}  // namespace te
+}  // namespace tbbt

@@ -157,3 +157,37 @@ def test_bulge_chase_shape_limits_on_the_host(L):
     assert L.tbbt_bulge_chase_z(p, 119, 200, 118, p, p, p, p, None) == ENOTSUP
     assert L.tbbt_bulge_chase_d(p, 129, 200, 129, p, p, p, p, None) == EINVAL  # nbw > 128
     assert L.tbbt_bulge_chase_d(p, 4, 0, 3, None, None, None, None, None) == 0  # n = 0: nothing to do
+
+
+def test_tridiag_eig_argument_checks(L):
+    # rejected (or a no-op) on the host, before any CUDA call
+    buf = (ctypes.c_double * 8)()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    EINVAL = 1
+    f = L.tbbt_tridiag_eig
+    assert f(p, p, -1, 0, p, p, 1, 0, None) == EINVAL  # n < 0
+    assert f(p, p, 10, 11, p, p, 10, 0, None) == EINVAL  # nev > n
+    assert f(p, p, 10, -1, p, p, 10, 0, None) == EINVAL  # nev < 0
+    assert f(p, p, 10, 5, p, p, 9, 0, None) == EINVAL  # ldx < n
+    assert f(p, p, 10, 5, p, p, 10, 7, None) == EINVAL  # xtype
+    assert f(None, p, 10, 5, p, p, 10, 0, None) == EINVAL  # null d
+    assert f(p, None, 10, 5, p, p, 10, 0, None) == EINVAL  # null e with n > 1
+    assert f(p, p, 10, 5, None, p, 10, 0, None) == EINVAL  # null w
+    assert f(p, p, 10, 5, p, None, 10, 0, None) == EINVAL  # null x
+    odd = ctypes.c_void_p(ctypes.addressof(buf) + 8)
+    assert f(p, p, 10, 5, p, odd, 10, 1, None) == EINVAL  # complex x not 16-byte aligned
+    assert f(None, None, 10, 0, None, None, 10, 0, None) == 0  # nev = 0: nothing to do
+    assert f(None, None, 0, 0, None, None, 1, 0, None) == 0  # n = 0
+
+
+def test_fp64_probe_argument_checks(L):
+    buf = (ctypes.c_double * 8)()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    fl = ctypes.c_double()
+    EINVAL = 1
+    f = L.tbbt_fp64_probe
+    assert f(2, 1, 32, 1, p, ctypes.byref(fl), None) == EINVAL  # kind
+    assert f(0, 0, 32, 1, p, ctypes.byref(fl), None) == EINVAL  # blocks
+    assert f(0, 1, 48, 1, p, ctypes.byref(fl), None) == EINVAL  # threads not a multiple of 32
+    assert f(0, 1, 32, 0, p, ctypes.byref(fl), None) == EINVAL  # iters
+    assert f(0, 1, 32, 1, None, ctypes.byref(fl), None) == EINVAL  # sink
