@@ -1224,6 +1224,8 @@ tbbt_status tridiag_eig_impl(const double *d, const double *e, int64_t n, int64_
     if (cudaGetLastError() != cudaSuccess) { rs = TBBT_ECUDA; break; }
     te::te_invit_kernel<<<(unsigned)((nev + te::INVIT_THREADS - 1) / te::INVIT_THREADS), te::INVIT_THREADS, 0, s>>>(A);
     if (cudaGetLastError() != cudaSuccess) { rs = TBBT_ECUDA; break; }
+    te::te_tight_kernel<<<(unsigned)nev, te::TIGHT_THREADS, 0, s>>>(A);
+    if (cudaGetLastError() != cudaSuccess) { rs = TBBT_ECUDA; break; }
     dim3 tg((unsigned)((n + 31) / 32), (unsigned)((nev + 31) / 32));
     te::te_transpose_kernel<<<tg, dim3(32, 8), 0, s>>>(A.y, (int32_t)n, (int32_t)nev, xr, ldr);
     if (cudaGetLastError() != cudaSuccess) { rs = TBBT_ECUDA; break; }

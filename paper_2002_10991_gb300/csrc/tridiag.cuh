@@ -16,8 +16,14 @@
 //     pseudo-random start, normalised after each. Factors and iterates are
 //     stored [row][vector], so each step of the recurrences is one coalesced
 //     access across the vectors of a warp.
-//  4. te_transpose_kernel: [row][vector] -> column-major X.
-//  5. te_reorth_kernel: modified Gram-Schmidt (twice) inside each cluster of
+//  4. te_tight_kernel: in groups of eigenvalues closer than TIGHT_TOL ||T||,
+//     independent iterations from nearly equal shifts converge to nearly
+//     parallel vectors, and orthogonalising those afterwards would amplify
+//     their errors. There every vector after the first is iterated again,
+//     its iterate orthogonalised against the group's earlier vectors after
+//     every solve (a block per group; the solves run on one thread).
+//  5. te_transpose_kernel: [row][vector] -> column-major X.
+//  6. te_reorth_kernel: modified Gram-Schmidt (twice) inside each cluster of
 //     eigenvalues closer than a fixed fraction of ||T||; a block per cluster.
 //     Inverse iteration leaves vectors of well-separated eigenvalues
 //     orthogonal to about eps ||T|| / gap; the clusters are where that bound
@@ -34,8 +40,11 @@ namespace te {
 constexpr int BOUNDS_THREADS = 256;
 constexpr int INVIT_THREADS = 128;
 constexpr int REORTH_THREADS = 256;
+constexpr int TIGHT_THREADS = 256;
 // eigenvalues closer than this fraction of ||T|| (chained) form a cluster
 constexpr double CLUSTER_TOL = 1e-4;
+// eigenvalues closer than this fraction of ||T|| (chained) form a tight group
+constexpr double TIGHT_TOL = 1e-9;
 // solves of inverse iteration per vector
 constexpr int INVIT_STEPS = 3;
 
@@ -165,6 +174,40 @@ struct InvitArgs {
   unsigned char *piv;
 };
 
+// One solve of inverse iteration for vector k, in place on its iterate:
+// y <- U^-1 L^-1 P y with the factors of T - w_k I. Returns max |y_i|.
+__device__ __forceinline__ double invit_solve(const InvitArgs &A, int32_t k) {
+  const int32_t n = A.n;
+  const size_t ld = (size_t)A.nev;
+  auto at = [&](int32_t i) { return (size_t)i * ld + (size_t)k; };
+  // forward: apply the row interchanges and multipliers to y
+  double yk = A.y[at(0)];
+  for (int32_t i = 0; i + 1 < n; ++i) {
+    double yn = A.y[at(i + 1)];
+    const double m = A.lm[at(i)];
+    if (A.piv[at(i)]) {
+      const double t = yk;
+      yk = yn;
+      yn = t - m * yk;
+    } else {
+      yn = yn - m * yk;
+    }
+    A.y[at(i)] = yk;
+    yk = yn;
+  }
+  A.y[at(n - 1)] = yk;
+  // back substitution with U (diagonal, two super-diagonals)
+  double x1 = 0.0, x2 = 0.0, amax = 0.0;
+  for (int32_t i = n - 1; i >= 0; --i) {
+    const double x = (A.y[at(i)] - A.u1[at(i)] * x1 - A.u2[at(i)] * x2) * A.u0[at(i)];
+    A.y[at(i)] = x;
+    amax = fmax(amax, fabs(x));
+    x2 = x1;
+    x1 = x;
+  }
+  return amax;
+}
+
 // Eigenvector k of T by inverse iteration (one thread per vector).
 __global__ void te_invit_kernel(InvitArgs A) {
   const int32_t k = (int32_t)(blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
@@ -220,32 +263,7 @@ __global__ void te_invit_kernel(InvitArgs A) {
     A.y[at(i)] = (double)(r >> 11) * (2.0 / 9007199254740992.0) - 1.0;
   }
   for (int step = 0; step < INVIT_STEPS; ++step) {
-    // forward: apply the row interchanges and multipliers to y
-    double yk = A.y[at(0)];
-    for (int32_t i = 0; i + 1 < n; ++i) {
-      double yn = A.y[at(i + 1)];
-      const double m = A.lm[at(i)];
-      if (A.piv[at(i)]) {
-        const double t = yk;
-        yk = yn;
-        yn = t - m * yk;
-      } else {
-        yn = yn - m * yk;
-      }
-      A.y[at(i)] = yk;
-      yk = yn;
-    }
-    A.y[at(n - 1)] = yk;
-    // back substitution with U (diagonal, two super-diagonals), tracking the
-    // largest magnitude
-    double x1 = 0.0, x2 = 0.0, amax = 0.0;
-    for (int32_t i = n - 1; i >= 0; --i) {
-      const double x = (A.y[at(i)] - A.u1[at(i)] * x1 - A.u2[at(i)] * x2) * A.u0[at(i)];
-      A.y[at(i)] = x;
-      amax = fmax(amax, fabs(x));
-      x2 = x1;
-      x1 = x;
-    }
+    const double amax = invit_solve(A, k);
     // normalise: scale by the largest entry first (no overflow in the sum)
     const double s = amax > 0.0 ? 1.0 / amax : 1.0;
     double ss = 0.0;
@@ -266,6 +284,61 @@ __global__ void te_invit_kernel(InvitArgs A) {
       }
     }
     for (int32_t i = 0; i < n; ++i) A.y[at(i)] *= f * sgn;
+  }
+}
+
+__device__ __forceinline__ double block_sum(double v, double *red);
+
+// Tight groups (eigenvalues chained by gaps below TIGHT_TOL ||T||) that
+// start at vector blockIdx.x: vectors j0+1 .. j1-1 are iterated again from a
+// new pseudo-random start, and after every solve the iterate is
+// orthogonalised (twice) against the group's earlier vectors and
+// normalised. Blocks at no group start, or of one-vector groups, return at
+// once. Works on the [row][vector] iterates.
+__global__ void te_tight_kernel(InvitArgs A) {
+  __shared__ double red[TIGHT_THREADS / 32];
+  __shared__ double s_scale;
+  const int32_t j0 = blockIdx.x, nev = A.nev, n = A.n;
+  const double tol = TIGHT_TOL * A.bounds->tnorm;
+  if (j0 > 0 && A.w[j0] - A.w[j0 - 1] < tol) return;  // not a group start
+  int32_t j1 = j0 + 1;
+  while (j1 < nev && A.w[j1] - A.w[j1 - 1] < tol) ++j1;
+  if (j1 - j0 < 2) return;
+  const size_t ld = (size_t)nev;
+  for (int32_t c = j0 + 1; c < j1; ++c) {
+    double *yc = A.y + c;  // element i at yc[i * ld]
+    const uint64_t key = mix64(0x7E5D1C0B3A29ull ^ ((uint64_t)c * 0x9E3779B97F4A7C15ull));
+    for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const uint64_t r = mix64(key + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull);
+      yc[(size_t)i * ld] = (double)(r >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+    }
+    __syncthreads();
+    for (int step = 0; step < INVIT_STEPS; ++step) {
+      if (threadIdx.x == 0) {
+        const double amax = invit_solve(A, c);
+        s_scale = amax > 0.0 ? 1.0 / amax : 1.0;
+      }
+      __syncthreads();
+      const double sc = s_scale;
+      for (int32_t i = threadIdx.x; i < n; i += blockDim.x) yc[(size_t)i * ld] *= sc;
+      __syncthreads();
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int32_t p = j0; p < c; ++p) {
+          const double *yp = A.y + p;
+          double s = 0.0;
+          for (int32_t i = threadIdx.x; i < n; i += blockDim.x) s += yp[(size_t)i * ld] * yc[(size_t)i * ld];
+          const double dot = block_sum(s, red);
+          for (int32_t i = threadIdx.x; i < n; i += blockDim.x) yc[(size_t)i * ld] -= dot * yp[(size_t)i * ld];
+          __syncthreads();
+        }
+      }
+      double s = 0.0;
+      for (int32_t i = threadIdx.x; i < n; i += blockDim.x) s += yc[(size_t)i * ld] * yc[(size_t)i * ld];
+      const double nrm = sqrt(block_sum(s, red));
+      const double f = nrm > 0.0 ? 1.0 / nrm : 0.0;
+      for (int32_t i = threadIdx.x; i < n; i += blockDim.x) yc[(size_t)i * ld] *= f;
+      __syncthreads();
+    }
   }
 }
 
