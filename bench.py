@@ -119,10 +119,15 @@ B2F_WORKLOADS = {"b2f-real-n8192-b64-nev4096": (8192, 64, 4096, False, I.SEED_BA
                  "b2f-real-n4096-b64-nev4096": (4096, 64, 4096, False, I.SEED_BASE + 12)}
 
 
+# tridiagonal eigensolver on the GPU (Eq. 6c): the T of a workload's band, nev lowest eigenpairs
+TRIDIAG_WORKLOADS = {"tridiag-real-n8192-nev4096": "real-n8192-b64-dft",
+                     "tridiag-real-n32768-nev9830": "real-n32768-b64-dft"}
+
+
 def set_workload(name: str):
     global WORKLOAD
     if name not in I.WORKLOADS and name != BATCH_WORKLOAD and name not in BULGE_WORKLOADS and \
-            name not in B2F_WORKLOADS:
+            name not in B2F_WORKLOADS and name not in TRIDIAG_WORKLOADS:
         raise SystemExit(f"unknown workload {name}")
     WORKLOAD = name
 
@@ -188,6 +193,65 @@ def b2f_bench(args):
                          "sample": f"{ncs} of {nev} columns"},
         "parity": {"max_abs_err_vs_oracle": err, "columns": len(cols)},
         "gpu_launches": 2 * args.steps, "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def tridiag_bench(args):
+    """Tridiagonal eigensolver (Eq. 6c) on the GPU for the nev lowest
+    eigenpairs of the T that the GPU bulge chase makes of a workload's band:
+    time per call; eigenvalues against LAPACK's bisection on the host
+    (scipy, timed as the host baseline); residual and orthogonality of the
+    vectors on the device."""
+    import torch
+    from scipy.linalg import eigvalsh_tridiagonal
+
+    import paper_2002_10991_gb300 as P
+
+    torch.cuda.set_device(0)
+    src = TRIDIAG_WORKLOADS[WORKLOAD]
+    w_ = I.WORKLOADS[src]
+    n, b, nev = w_["n"], w_["b"], w_["nev"]
+    W = I.band_for(src)
+    _, _, d, e = P.bulge_chase(torch.from_numpy(np.ascontiguousarray(W.T)).cuda().t())
+    P.stream_check()
+    for _ in range(max(args.warmup, 1)):
+        w, X = P.tridiag_eig(d, e, nev)
+    P.stream_check()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clocks:
+        e0.record(stream)
+        for _ in range(args.steps):
+            w, X = P.tridiag_eig(d, e, nev)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    P.stream_check()
+    ms = e0.elapsed_time(e1) / args.steps
+    dh, eh = d.cpu().numpy(), e.cpu().numpy()
+    t0 = time.perf_counter()
+    lam = eigvalsh_tridiagonal(dh, eh, select="i", select_range=(0, nev - 1))
+    host_s = time.perf_counter() - t0
+    r = np.abs(dh).copy()
+    r[1:] += np.abs(eh)
+    r[:-1] += np.abs(eh)
+    tn = float(r.max())
+    TX = d[:, None] * X
+    TX[1:] += e[:, None] * X[:-1]
+    TX[:-1] += e[:, None] * X[1:]
+    res = torch.linalg.vector_norm(TX - X * w[None, :], dim=0).max().item() / tn
+    del TX
+    G = X.t() @ X
+    G.diagonal().sub_(1.0)
+    line = {
+        "metric": "tridiagonal eigensolver time (nev lowest eigenpairs)", "value": ms, "unit": "ms", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "nev": nev, "tridiagonal": f"GPU bulge chase of the {src} band"},
+        "parity": {"max_abs_eig_err_vs_lapack_over_tnorm": float(np.abs(w.cpu().numpy() - lam).max() / tn),
+                   "residual_max_over_tnorm": res, "orthogonality_max": G.abs().max().item()},
+        "host_baseline": {"value": host_s * 1e3, "unit": "ms", "kind": "LAPACK eigenvalues only (scipy stebz)"},
+        "gpu_launches": 5 * args.steps, "clocks": clocks.summary(),
     }
     print(json.dumps(line), flush=True)
 
@@ -726,14 +790,25 @@ def split_accuracy(name: str):
     ev[1].record(stream)
     w, X = P.tridiag_eig(d, e, nev)
     ev[2].record(stream)
+    X64 = X.clone()
     sp = P.Plan(False, n, b, nev, variant=VARIANTS["split-tc"])
     sp.set_reflectors(v, tau)
     sp.execute(X)
     ev[3].record(stream)
     P.stream_check()
     sp.close()
+    # the same chain with the FP64 back-transform, for comparison
+    P.trans_ev_tridi_to_band(v, tau, n, b, nev, X64)
+    P.stream_check()
+    P.release_cache()
     del band, v, tau
+    q64 = eigen_quality(W, w, X64)
+    diff = (X - X64).abs().max().item()
+    del X64
     q = eigen_quality(W, w, X)
+    q["fp64_back_transform"] = {k: q64[k] for k in ("residual_max_over_norm", "max_abs_column_norm_minus_1",
+                                                     "orthogonality_max")}
+    q["max_abs_diff_split_vs_fp64"] = diff
     q.update({"chain": "GPU bulge chase -> GPU tridiagonal eigensolver -> split-tc back-transform",
               "workload_band": name, "n": n, "nbw": b, "nev": nev,
               "ms": {"bulge_chase": ev[0].elapsed_time(ev[1]), "tridiag_eig": ev[1].elapsed_time(ev[2]),
@@ -839,6 +914,9 @@ def main():
         return
     if WORKLOAD in B2F_WORKLOADS:
         b2f_bench(args)
+        return
+    if WORKLOAD in TRIDIAG_WORKLOADS:
+        tridiag_bench(args)
         return
     world, rank, local = dist_setup()
 
@@ -1015,7 +1093,7 @@ def main():
         for nm in names:
             torch.cuda.empty_cache()
             if nm == BATCH_WORKLOAD:
-                m = batch_measure(args.extra_steps)
+                m = batch_measure(args.extra_steps, autotune=True)
                 m["of_fp64_peak"] = m["batched"]["tflops"] / peak_at_clock(probe, m["clocks"]["sm_mhz"])
             elif nm == "real-n512-b32-uniform":
                 m = measure_fp64(nm, max(args.extra_steps, 5), 2, parity_cols=512)

@@ -203,11 +203,13 @@ typedef struct {
   int32_t sweeps_per_block;        /* 0 = 4 (4 or 8) */
   int32_t stages_per_step_real;    /* 0 = 16 */
   int32_t stages_per_step_complex; /* 0 = 4; defaults are lowered until two blocks fit an SM */
-  /* Nonzero: time candidate geometries at creation on scratch copies of
-   * every q (the caller's data are not touched) and keep the fastest. Results
-   * are cached per process and GPU and, if autotune_cache (or the environment
-   * variable TBBT_AUTOTUNE_CACHE) names a file, appended to it and read back
-   * by later processes. Tuning runs the whole batch several times. */
+  /* Nonzero: time candidate geometries at creation and keep the fastest.
+   * Candidates run on a proxy of the batch (every problem with 1/16 of its
+   * columns, in whole 32-column strips, on scratch copies; the caller's data
+   * are not touched): six candidates cost about 3/4 of one execution of
+   * the batch. Results are cached per process and GPU and, if
+   * autotune_cache (or the environment variable TBBT_AUTOTUNE_CACHE) names
+   * a file, appended to it and read back by later processes. */
   int32_t autotune;
   const char *autotune_cache;
   int32_t wait_timeout_ms; /* 0 = 20000, see tbbt_options */

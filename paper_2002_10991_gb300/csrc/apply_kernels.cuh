@@ -211,6 +211,15 @@ __device__ __forceinline__ int wait_released(const ApplyArgs &a, const int *flag
   return wait_released_raw(a.err, a.timeout_ns, flag, need);
 }
 
+// Element of ring slot sl (row sl of the ring) and strip column c. The
+// lane-pair complex kernel (SWZ) moves the columns of odd slots by four
+// (64 bytes): the two lanes of a pair touch adjacent rows of one column at
+// the same time, which would otherwise fall on the same shared-memory banks.
+template <bool SWZ>
+__device__ __forceinline__ int64_t ring_slot(int32_t sl, int32_t c) {
+  return (int64_t)sl * 32 + (SWZ ? (c ^ ((sl & 1) << 2)) : c);
+}
+
 template <typename T>
 __device__ __forceinline__ T ld_cg(const T *p);
 template <>
@@ -225,7 +234,7 @@ __device__ __forceinline__ zdouble ld_cg<zdouble>(const zdouble *p) {
 
 // Rows [r0, r1) of the strip, global -> ring, synchronously (L2 path: rows
 // may have been written by another SM). Columns >= nev read as zero.
-template <typename T>
+template <typename T, bool SWZ = false>
 __device__ __forceinline__ void load_rows_now(const ApplyArgs &a, T *ring, int32_t r0, int32_t r1, int32_t c0) {
   const int32_t nrows = r1 - r0;
   if (nrows <= 0) return;
@@ -234,13 +243,13 @@ __device__ __forceinline__ void load_rows_now(const ApplyArgs &a, T *ring, int32
     int32_t c = idx / nrows;
     int32_t r = r0 + (idx - c * nrows);
     int32_t col = c0 + c;
-    ring[(int64_t)(r % a.ring) * 32 + c] = col < a.nev ? ld_cg(q + (int64_t)col * a.ldq + r) : Arith<T>::zero();
+    ring[ring_slot<SWZ>(r % a.ring, c)] = col < a.nev ? ld_cg(q + (int64_t)col * a.ldq + r) : Arith<T>::zero();
   }
 }
 
 // The same split in two: issue the loads into registers now, write them to
 // the ring after the step's arithmetic (hides the memory latency).
-template <typename T>
+template <typename T, bool SWZ = false>
 struct RowPrefetch {
   T val[kMaxPrefetch];
   __device__ __forceinline__ void issue(const ApplyArgs &a, int32_t r0, int32_t r1, int32_t c0) {
@@ -265,14 +274,14 @@ struct RowPrefetch {
       if (nrows > 0 && idx < nrows * 32) {
         int32_t c = idx / nrows;
         int32_t r = r0 + (idx - c * nrows);
-        ring[(int64_t)(r % a.ring) * 32 + c] = val[i];
+        ring[ring_slot<SWZ>(r % a.ring, c)] = val[i];
       }
     }
   }
 };
 
 // Rows [r0, r1): ring -> global.
-template <typename T>
+template <typename T, bool SWZ = false>
 __device__ __forceinline__ void store_rows(const ApplyArgs &a, const T *ring, int32_t r0, int32_t r1, int32_t c0) {
   const int32_t nrows = r1 - r0;
   if (nrows <= 0) return;
@@ -282,7 +291,7 @@ __device__ __forceinline__ void store_rows(const ApplyArgs &a, const T *ring, in
     int32_t c = idx / nrows;
     int32_t r = r0 + (idx - c * nrows);
     int32_t col = c0 + c;
-    if (col < a.nev) q[(int64_t)col * a.ldq + r] = ring[(int64_t)(r % a.ring) * 32 + c];
+    if (col < a.nev) q[(int64_t)col * a.ldq + r] = ring[ring_slot<SWZ>(r % a.ring, c)];
   }
 }
 
@@ -333,48 +342,51 @@ __device__ __forceinline__ void apply_one(T *col, int32_t ring, int32_t r, int32
   }
 }
 
-// Eq. 8 for one reflector on one complex column, by a pair of lanes: lane h
-// of the pair takes the rows [h ? Lh : 0, h ? L : Lh) of the window (Lh =
-// ceil(L / 2)), and the two partial sums of v^H x are added with one exchange
-// inside the pair (both lanes form the same sum: addition commutes). Each
-// lane's dependent chain is half as long, and a 32-column strip takes two
-// warps per sweep, two per SM sub-partition.
-__device__ __forceinline__ void apply_pair(zdouble *col, int32_t ring, int32_t r, int32_t L, const zdouble *ent,
-                                           int h) {
-  const int32_t Lh = (L + 1) >> 1;
-  const int32_t t0 = h ? Lh : 1, t1 = h ? L : Lh;
-  const int32_t base = r % ring;
-  zdouble s = h ? zdouble{0.0, 0.0} : col[(int64_t)base * 32];
+// Eq. 8 for one reflector on one complex column (strip column c), by a pair
+// of lanes: lane h of the pair takes the rows t = h, h + 2, h + 4, ... of
+// the window (v_0 = 1, so the row-0 term of lane 0 is x_0 itself), and the
+// two partial sums of v^H x are added with one exchange inside the pair
+// (both lanes form the same sum: addition commutes). Each lane's dependent
+// chain is half as long, and a 32-column strip takes two warps per sweep,
+// two per SM sub-partition. The ring is swizzled (ring_slot<true>): at every
+// step the lanes of a pair touch adjacent rows, on different banks.
+__device__ __forceinline__ void apply_pair(zdouble *ring, int32_t nring, int32_t c, int32_t r, int32_t L,
+                                           const zdouble *ent, int h) {
+  const int32_t base = r % nring;
+  const int32_t t0 = h ? 1 : 2;
   int32_t sl0 = base + t0;
-  if (sl0 >= ring) sl0 -= ring;
+  if (sl0 >= nring) sl0 -= nring;
+  zdouble s = h ? zdouble{0.0, 0.0} : ring[ring_slot<true>(base, c)];
   {
     int32_t sl = sl0;
 #pragma unroll 4
-    for (int32_t t = t0; t < t1; ++t) {
-      Arith<zdouble>::dot(s, ent[t], col[(int64_t)sl * 32]);
-      sl = (sl + 1 == ring) ? 0 : sl + 1;
+    for (int32_t t = t0; t < L; t += 2) {
+      Arith<zdouble>::dot(s, ent[t], ring[ring_slot<true>(sl, c)]);
+      sl += 2;
+      if (sl >= nring) sl -= nring;
     }
   }
   s.re += __shfl_xor_sync(0xffffffffu, s.re, 1);
   s.im += __shfl_xor_sync(0xffffffffu, s.im, 1);
   const zdouble u = Arith<zdouble>::scale(ent[0], s);
   if (!h) {
-    zdouble x0 = col[(int64_t)base * 32];
+    zdouble x0 = ring[ring_slot<true>(base, c)];
     Arith<zdouble>::sub(x0, u);
-    col[(int64_t)base * 32] = x0;
+    ring[ring_slot<true>(base, c)] = x0;
   }
   {
     int32_t sl = sl0;
 #pragma unroll 4
-    for (int32_t t = t0; t < t1; ++t) {
-      zdouble x = col[(int64_t)sl * 32];
+    for (int32_t t = t0; t < L; t += 2) {
+      zdouble x = ring[ring_slot<true>(sl, c)];
       Arith<zdouble>::axpy(x, u, ent[t]);
-      col[(int64_t)sl * 32] = x;
-      sl = (sl + 1 == ring) ? 0 : sl + 1;
+      ring[ring_slot<true>(sl, c)] = x;
+      sl += 2;
+      if (sl >= nring) sl -= nring;
     }
   }
-  // the next reflector starts one row up: its upper lane reads a row this
-  // reflector's lower lane just wrote
+  // the next reflector starts one row up: each lane then takes the rows the
+  // other lane just wrote
   __syncwarp();
 }
 
@@ -474,7 +486,9 @@ __device__ __forceinline__ bool process_unit(const ApplyArgs &a, int32_t e, int3
   const int li = BW < 0 ? lane + 32 * cs : lane, nl = BW < 0 ? 64 : 32;
   const StoreGeom &g = a.g;
   T *vbuf_w = vbuf + (int64_t)w * 2 * a.NB * a.ldv;
-  T *mycol = BW < 0 ? ring + 16 * cs + (lane >> 1) : ring + lane;
+  constexpr bool SWZ = BW < 0;  // the lane-pair kernel's ring is swizzled
+  T *mycol = ring + lane;       // (shared-memory window and register-window kernels)
+  const int32_t pcol = 16 * cs + (lane >> 1);  // lane pairs: strip column of this pair
   double xw[BW > 0 ? BW : 1];  // register window of the lane's column (BW > 0)
   (void)xw;
   const Epoch ep = make_epoch(g, e, a.G, a.NB);
@@ -485,18 +499,18 @@ __device__ __forceinline__ bool process_unit(const ApplyArgs &a, int32_t e, int3
   __syncthreads();
   bool abandoned = *s_stop != 0;
   if (!abandoned) {
-    load_rows_now<T>(a, ring, top, g.n, c0);
+    load_rows_now<T, SWZ>(a, ring, top, g.n, c0);
     load_reflectors<T>(a, ep, vbuf_w, w, 0, li, nl);
     cp_async_wait_all();
     __syncthreads();
     int32_t released = g.n;  // rows >= released are back in global memory
-    RowPrefetch<T> pf;
+    RowPrefetch<T, SWZ> pf;
     for (int32_t t = 0; t < ep.nsteps; ++t) {
       // rows no warp touches from step t on go back to global memory
       int32_t live = rows_live_max(g, ep, t);
       int32_t rel = live + 1 > top ? live + 1 : top;
       if (rel < released) {
-        store_rows<T>(a, ring, rel, released, c0);
+        store_rows<T, SWZ>(a, ring, rel, released, c0);
         released = rel;
       }
       // rows of step t+1 must have been released by the previous epoch
@@ -521,7 +535,7 @@ __device__ __forceinline__ bool process_unit(const ApplyArgs &a, int32_t e, int3
           apply_stages_regwin<BW>(xw, mycol, a.ring, g, j, hi, lo, vb, sig, a.ldv);
         } else if constexpr (BW < 0) {
           for (int32_t s = hi; s >= lo; --s)
-            apply_pair(mycol, a.ring, g.row(s, j), g.len(s, j), vb + (int64_t)(sig - s) * a.ldv, lane & 1);
+            apply_pair(ring, a.ring, pcol, g.row(s, j), g.len(s, j), vb + (int64_t)(sig - s) * a.ldv, lane & 1);
         } else {
           for (int32_t s = hi; s >= lo; --s)
             apply_one<T>(mycol, a.ring, g.row(s, j), g.len(s, j), vb + (int64_t)(sig - s) * a.ldv);
@@ -534,7 +548,7 @@ __device__ __forceinline__ bool process_unit(const ApplyArgs &a, int32_t e, int3
     }
     if (!abandoned) {
       // the rest of the strip is final for this epoch
-      store_rows<T>(a, ring, top, released, c0);
+      store_rows<T, SWZ>(a, ring, top, released, c0);
       __syncthreads();
       if (threadIdx.x == 0 && publish) st_release(myflag, top);
     }

@@ -379,15 +379,24 @@ tbbt_status tbbt_batch_create(tbbt_batch **out, int32_t count, const tbbt_proble
     }
     if (!have && read_tune_file(path, sig, &best)) have = true;
     if (!have) {
-      // scratch copies of every q, so that timing leaves the caller's data alone
-      std::vector<void *> scratch(b->probs.size(), nullptr);
-      std::vector<int64_t> sld(b->probs.size(), 1);
+      // Candidates are timed on a proxy of the batch: the same problems with
+      // 1/16 of their columns (whole 32-column strips, at least one), on
+      // scratch copies of those columns (the caller's data stay untouched).
+      // Every unit's work is unchanged and there are still far more units
+      // than resident blocks, so the proxy ranks geometries as the batch
+      // does, at a sixteenth of the cost.
+      tbbt_batch px;
+      px.probs = b->probs;
+      px.timeout_ns = b->timeout_ns;
+      std::vector<void *> scratch(px.probs.size(), nullptr);
+      std::vector<int64_t> sld(px.probs.size(), 1);
       bool ok = true;
-      for (size_t i = 0; i < b->probs.size() && ok; ++i) {
-        const auto &h = b->probs[i];
+      for (size_t i = 0; i < px.probs.size() && ok; ++i) {
+        auto &h = px.probs[i];
         const size_t es = elem_size(h.p.dtype);
         sld[i] = std::max<int64_t>(1, h.p.n);
         if (h.p.nev == 0) continue;
+        h.p.nev = std::min<int64_t>(h.p.nev, std::max<int64_t>(32, (h.p.nev / 16 + 31) / 32 * 32));
         ok = cudaMalloc(&scratch[i], (size_t)sld[i] * h.p.nev * es) == cudaSuccess &&
              cudaMemcpy2D(scratch[i], (size_t)sld[i] * es, h.p.q, (size_t)h.p.ldq * es, (size_t)h.p.n * es,
                           (size_t)h.p.nev, cudaMemcpyDeviceToDevice) == cudaSuccess;
@@ -396,7 +405,7 @@ tbbt_status tbbt_batch_create(tbbt_batch **out, int32_t count, const tbbt_proble
       const BatchGeom cands[] = {{4, 8, 8}, {4, 8, 4}, {4, 16, 4}, {4, 4, 4}, {8, 8, 4}, {8, 16, 8}};
       for (const BatchGeom &c : cands) {
         if (!ok) break;
-        double ms = batch_time_candidate(b, c, scratch, sld);
+        double ms = batch_time_candidate(&px, c, scratch, sld);
         if (ms > 0 && (best_ms < 0 || ms < best_ms)) {
           best_ms = ms;
           best = c;

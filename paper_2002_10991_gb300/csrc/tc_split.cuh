@@ -30,7 +30,10 @@
 //
 // Exactness (digit positions 61 - 8k, k = 1..6, balanced digits): Z is fixed
 // point with |Z| <= 2^61 (first digit |d| <= 256, others <= 128); V', U' and W
-// are scaled to |x| <= 2^60 so that all their digits are <= 128. A level sums
+// are scaled to |x| <= 2^60 so that all their digits are <= 128. Before its
+// digits are taken, each column's window of Z is shifted left by the most
+// bits that keep |Z| < 2^61 and its 1-norm within 2^66 (the bound that keeps
+// W in 64-bit range), so the digits hold the window's leading bits. A level sums
 // at most 6 digit products over K terms: GEMM1 (K <= 96) stays below 2^24 and
 // is read with an exact float->int conversion; GEMM2 (K = 32) stays below 2^22,
 // where the add-magic-number conversion is exact.
@@ -93,8 +96,10 @@ struct Geo {
   static constexpr int OFF_V = OFF_W + S * WDIG;
   static constexpr int OFF_U = OFF_V + VBYTES;
   static constexpr int OFF_STG = (OFF_U + UBYTES + 1023) / 1024 * 1024;  // two swizzled boxes [c][16 rows]
-  static constexpr int OFF_KMX = OFF_STG + 2 * WS * STG_ROWS * 8;      // [NSUB][WS] partial maxima of |W|
-  static constexpr int SMEM = OFF_KMX + NSUB * WS * 8 + 1024;  // + room to align the base to 1024 bytes
+  // [NSUB][WS] partial maxima of |W|; before that, in the same place,
+  // [2 NSUB][WS] partial maxima and 1-norms of the window's Z
+  static constexpr int OFF_KMX = OFF_STG + 2 * WS * STG_ROWS * 8;
+  static constexpr int SMEM = OFF_KMX + 2 * NSUB * WS * 8 + 1024;  // + room to align the base to 1024 bytes
 };
 
 // byte offset of element (row, k) of a K-major operand with kt values of k per
@@ -312,7 +317,7 @@ __device__ __forceinline__ void tmem_z_digit(int k, uint32_t taddr, const int64_
 // exact float -> int for integer values below 2^22 in magnitude
 __device__ __forceinline__ int32_t f2i_small(float v) { return __float_as_int(v + 12582912.0f) - 0x4B400000; }
 __device__ __forceinline__ int64_t shl_signed(int64_t x, int s) {
-  return s >= 0 ? (int64_t)((uint64_t)x << s) : (x >> (-s));
+  return s >= 0 ? (int64_t)((uint64_t)x << s) : (x >> min(-s, 63));
 }
 __device__ __forceinline__ int64_t shl8_add(int64_t h, int32_t v) { return (int64_t)((uint64_t)h << 8) + v; }
 
@@ -845,6 +850,48 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
             if (!mbar_wait(&bars.blk, (n_blk - 1) & 1, &s_abort, a.err, a.timeout_ns)) break;
             tc_fence_after();
           }
+          // ---- shift of this block's window, per column: the digits take the
+          // leading bits of Z 2^zsh, not of Z (Z's fixed point is scaled to the
+          // column's norm bound, far above the entries of a delocalised
+          // column, whose low bits the digits would drop). zsh keeps every
+          // entry below 2^61 (the digits' range) and the window's 1-norm
+          // within 2^66, so that W = V'^T Z 2^-64 stays within 2^62 for any
+          // reflector (|V'| <= 2^60).
+          // Bounds from the high words: Z = z - C has high word h = hi(z) -
+          // hi(C) - (borrow 0 or 1), so |Z| < (|hi(z) - hi(C)| + 2) 2^32 =: m 2^32.
+          int zsh;
+          {
+            constexpr int32_t CHI = (int32_t)(kDigitOffset >> 32);
+            uint32_t mz = 0, sz = 0;
+#pragma unroll
+            for (int i = 0; i < RT; ++i) {
+              const int32_t h = (int32_t)((uint64_t)z[i] >> 32) - CHI;
+              const uint32_t m = (uint32_t)(h < 0 ? -h : h) + 2u;  // < 2^30
+              mz = m > mz ? m : mz;
+              sz += (m + 31u) >> 5;  // >= m / 32; 96 terms stay below 2^32
+            }
+            uint32_t *kz = reinterpret_cast<uint32_t *>(smem + D::OFF_KMX);
+            kz[sub * WS + col] = mz;
+            kz[(D::NSUB + sub) * WS + col] = sz;
+            named_sync(1, D::NMATH);
+            mz = 0;
+            sz = 0;
+#pragma unroll
+            for (int q = 0; q < D::NSUB; ++q) {
+              const uint32_t o = kz[q * WS + col];
+              mz = o > mz ? o : mz;
+              sz += kz[(D::NSUB + q) * WS + col];
+            }
+            // every |Z| < 2^(32 + bits(mz)); the 1-norm < sz 2^37 < 2^(37 + bits(sz))
+            const int zb = 32 + (32 - __clz((int)mz));
+            const int sb = 37 + (32 - __clz((int)sz));
+            zsh = min(min(FIX - zb, 66 - sb), 16);  // 16: more gains nothing at the column's scale
+            zsh = zsh > 0 ? zsh : 0;
+          }
+          if (zsh > 0) {
+#pragma unroll
+            for (int i = 0; i < RT; ++i) z[i] = (int64_t)((uint64_t)(z[i] - C) << zsh) + C;
+          }
           {
             const uint32_t zt = tmem + lane_base + ZA_COL + prow / 2;
 #pragma unroll
@@ -854,6 +901,10 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
               tc_fence_before();
               mbar_arrive(&bars.zfull[k - 1]);
             }
+          }
+          if (zsh > 0) {  // back to Z (exact: the low zsh bits are zero)
+#pragma unroll
+            for (int i = 0; i < RT; ++i) z[i] = ((z[i] - C) >> zsh) + C;
           }
           if (!ok) break;
           // ---- W = V'^T Z for my column and my reflector range
@@ -920,7 +971,7 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
           // T = P01 2^16 + P23 and T2 = P45 2^8 + a_6 (exact in 64 bits)
           if (!mbar_wait(&bars.c[p], n_blk & 1, &s_abort, a.err, a.timeout_ns)) break;
           tc_fence_after();
-          const int rs = 50 + gv - kcol;
+          const int rs = 50 + gv - kcol - zsh;
           const uint32_t dreg = tmem + lane_base + (p == 0 ? 0u : (uint32_t)REG_B) + RT * hf;
           constexpr int PR = (RT >= 16) ? 4 : 8;  // rows per piece (register budget)
 #pragma unroll

@@ -137,7 +137,8 @@ def test_batch_full_size_64_mixed_sampled_columns(P):
     P.stream_check()
     rng = np.random.default_rng(11)
     for (dv, dt, n, b, nev, q), (v, tau, X) in zip(probs, host):
-        cols = np.unique(np.concatenate([[0, nev - 1], rng.choice(nev, 1)]))
+        # 16 columns per problem: both ends, a strip boundary, the rest random
+        cols = np.unique(np.concatenate([[0, 31, 32, nev - 1], rng.choice(nev, 12, replace=False)]))
         got = q[:, torch.from_numpy(cols).cuda()].cpu().numpy()
         Zo = oracle.back_transform(v, tau, n, b, np.asfortranarray(X[:, cols]), nthreads=oracle.num_cpus())
         assert np.abs(got - Zo).max() <= TOL, (n, b, nev)
