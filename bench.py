@@ -677,7 +677,8 @@ def fp64_peak_bench(args):
 # one FP64 configuration: time, parity on a column sample, rate
 # ---------------------------------------------------------------------------
 
-def measure_fp64(name: str, steps: int, warmup: int, parity_cols: int = 8):
+def measure_fp64(name: str, steps: int, warmup: int, parity_cols: int = 8, sweeps_per_block: int = 0,
+                 stages_per_step: int = 0):
     """The plain FP64 path on one named workload: re-layout + apply per step,
     CUDA events on the calling stream, parity of a column sample against the
     oracle. Returns a dict (inputs built and freed here)."""
@@ -689,7 +690,7 @@ def measure_fp64(name: str, steps: int, warmup: int, parity_cols: int = 8):
     n, b, nev, cplx = w["n"], w["b"], w["nev"], w["complex_"]
     dv, dt = torch.from_numpy(v).cuda(), torch.from_numpy(tau).cuda()
     q = torch.from_numpy(X.T.copy()).cuda().t()
-    plan = P.Plan(cplx, n, b, nev)
+    plan = P.Plan(cplx, n, b, nev, sweeps_per_block=sweeps_per_block, stages_per_step=stages_per_step)
     cols, Xs = cpu_sample(v, tau, X, w, parity_cols, seed=3)
     plan.set_reflectors(dv, dt)
     plan.execute(q)
@@ -895,6 +896,9 @@ def main():
                          ", ".join(BULGE_WORKLOADS) + ") and the band -> full back-transformation (" +
                          ", ".join(B2F_WORKLOADS) + "))")
     ap.add_argument("--autotune", action="store_true", help="batched workload: tune the launch geometry first")
+    ap.add_argument("--geometry-sweep", default="",
+                    help="FP64 workloads: semicolon-separated sweeps_per_block,stages_per_step pairs, each timed "
+                         "(--steps steps after one warm-up) into one JSON line instead of the benchmark")
     ap.add_argument("--variant", default="fp64", choices=list(VARIANTS),
                     help="fp64: reflector-by-reflector FP64 kernel; split: WY blocks on BF16 tensor cores "
                          "with exact digit slices (real b=32/64, warp-level mma.sync); split-tc: the same "
@@ -917,6 +921,19 @@ def main():
         return
     if WORKLOAD in TRIDIAG_WORKLOADS:
         tridiag_bench(args)
+        return
+    if args.geometry_sweep:
+        import torch
+
+        torch.cuda.set_device(0)
+        out = {}
+        for pair in args.geometry_sweep.split(";"):
+            G, NB = (int(x) for x in pair.split(","))
+            m = measure_fp64(WORKLOAD, args.steps, 1, parity_cols=8, sweeps_per_block=G, stages_per_step=NB)
+            out[pair] = {"ms": m["apply_ms_avg"], "tflops": m["apply_tflops"], "launch": m["launch"],
+                         "parity": m["parity"]["max_abs_err_vs_oracle"], "clocks": m["clocks"]}
+        print(json.dumps({"metric": "launch geometry sweep", "config": {"workload": WORKLOAD}, "runs": out}),
+              flush=True)
         return
     world, rank, local = dist_setup()
 
