@@ -1142,6 +1142,15 @@ def main():
                "kind": "oracle",
                "sample": f"{len(cols)} of {nev} columns, all {len(tau)} reflectors",
                "parity_max_abs_vs_gpu": float(np.abs(Zo - gpu_cols).max())}
+        # the same oracle on one host thread, on the first 16 columns of the sample
+        import oracle
+
+        Z1 = np.asfortranarray(Xs[:, :16])
+        t0 = time.perf_counter()
+        oracle.back_transform(v, tau, n, b, Z1, nthreads=1)
+        t1 = time.perf_counter() - t0
+        cpu["single_thread"] = {"value": (16 if cplx else 4) * Z1.shape[1] * sum_l / t1 / 1e12, "unit": "TFLOP/s",
+                                "cores": 1, "sample": f"{Z1.shape[1]} of {nev} columns, all {len(tau)} reflectors"}
         if split:
             # the BF16 tensor-core form: FP64-equivalent algorithmic rate; its own roofline is the
             # tensor pipe (bf16 MMA issued per step), reported beside the FP64 reference

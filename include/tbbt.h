@@ -116,11 +116,11 @@ tbbt_status tbbt_release_cache(void);
 typedef struct tbbt_plan tbbt_plan;
 
 typedef struct {
-  /* Sweeps processed concurrently by one thread block (one warp each);
-   * 0 = choose automatically. */
+  /* Sweeps processed concurrently by one thread block (one warp each, two
+   * for complex data); 0 = choose automatically (4 real, 1 complex). */
   int32_t sweeps_per_block;
   /* Stages each warp applies between two block-wide synchronisations;
-   * 0 = choose automatically (at most 4 * sweeps_per_block). */
+   * 0 = choose automatically (8 real, 2 complex; at most 4 * sweeps_per_block). */
   int32_t stages_per_step;
   /* Limit of every in-kernel wait, in milliseconds; 0 = 20000. A wait that
    * runs out records TBBT_ETIMEOUT (see tbbt_stream_check); the kernel then

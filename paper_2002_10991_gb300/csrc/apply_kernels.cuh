@@ -467,6 +467,104 @@ __device__ __forceinline__ void apply_stages_regwin(double (&x)[B], double *ring
   }
 }
 
+// 16-byte shared-memory load the compiler may not merge or hoist (as lds_f64).
+__device__ __forceinline__ zdouble lds_z(const zdouble *p) {
+  double re, im;
+  asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];\n" : "=d"(re), "=d"(im) : "r"(smem_u32(p)));
+  return zdouble{re, im};
+}
+
+// Register window for complex data and b = 2H, a lane pair per column
+// (strip column c): lane h of the pair keeps rows r + H h .. r + H h + H - 1
+// of its column's window in registers, so the dot product and the update
+// run on registers, and the two halves of v^H x are added by one exchange
+// inside the pair. The window moves up one row per stage; the update runs
+// from the bottom of each half up and moves every element one register down:
+// the element that leaves the lower lane's half enters the upper lane's by
+// one exchange, the upper lane's last element leaves the window for the ring
+// (the next sweep reads it there), and the lower lane takes the new top row
+// from the ring at the next stage. Rows >= n are held as zeros and meet zero
+// reflector entries, so they stay zero and are never written.
+template <int H>
+__device__ __forceinline__ void apply_stages_regwin_pair(zdouble (&x)[H], zdouble *ring, int32_t nring, int32_t c,
+                                                         const StoreGeom &g, int32_t j, int32_t hi, int32_t lo,
+                                                         const zdouble *vb, int32_t sig, int32_t ldv, int h) {
+  constexpr int B = 2 * H;
+  constexpr int PF = 4;
+  const int32_t first = g.imax(j);
+  const zdouble one{1.0, 0.0};
+  for (int32_t s = hi; s >= lo; --s) {
+    const int32_t r = g.row(s, j);
+    if (s == first) {
+      // first stage of the sweep: fill this lane's half of the window
+      int32_t sl = (r + H * h) % nring;
+#pragma unroll
+      for (int32_t t = 0; t < H; ++t) {
+        x[t] = (r + H * h + t < g.n) ? ring[ring_slot<true>(sl, c)] : Arith<zdouble>::zero();
+        sl = (sl + 1 == nring) ? 0 : sl + 1;
+      }
+    } else if (h == 0) {
+      x[0] = ring[ring_slot<true>(r % nring, c)];  // the upper lane's x[0] came by exchange
+    }
+    const zdouble *ent = vb + (int64_t)(sig - s) * ldv;  // [tau, v_1, ..., v_{B-1}]
+    const zdouble *eh = ent + H * h;                       // this lane's entries: v_{H h + t}
+    // v^H x over this lane's half (v_0 = 1: the lower lane's first entry)
+    zdouble acc = Arith<zdouble>::zero();
+    {
+      zdouble v[PF];
+#pragma unroll
+      for (int k = 0; k < PF; ++k) v[k] = (k == 0 && h == 0) ? one : lds_z(eh + k);
+#pragma unroll
+      for (int32_t t = 0; t < H; ++t) {
+        const zdouble vt = v[t % PF];
+        if (t + PF < H) v[t % PF] = lds_z(eh + t + PF);
+        Arith<zdouble>::dot(acc, vt, x[t]);
+      }
+    }
+    acc.re += __shfl_xor_sync(0xffffffffu, acc.re, 1);
+    acc.im += __shfl_xor_sync(0xffffffffu, acc.im, 1);
+    const zdouble u = Arith<zdouble>::scale(lds_z(ent), acc);
+    if (s > 0) {
+      // bottom-up, entries v_{H h + H - 1} .. v_{H h}
+      zdouble w[PF];
+#pragma unroll
+      for (int k = 0; k < PF; ++k) w[k] = lds_z(eh + H - 1 - k);
+      zdouble out = x[H - 1];
+      Arith<zdouble>::axpy(out, u, w[0]);  // this half's last row leaves it
+      if (PF <= H - 1) w[0] = lds_z(eh + H - 1 - PF);
+#pragma unroll
+      for (int32_t k = 1; k <= H - 1; ++k) {  // element t = H - 1 - k moves to register t + 1
+        zdouble wk = w[k % PF];
+        if (k + PF <= H - 1) w[k % PF] = (h == 0 && H - 1 - k - PF == 0) ? one : lds_z(eh + H - 1 - k - PF);
+        if (h == 0 && k == H - 1) wk = one;  // v_0
+        zdouble xt = x[H - 1 - k];
+        Arith<zdouble>::axpy(xt, u, wk);
+        x[H - k] = xt;
+      }
+      zdouble in;
+      in.re = __shfl_xor_sync(0xffffffffu, out.re, 1);
+      in.im = __shfl_xor_sync(0xffffffffu, out.im, 1);
+      if (h == 1) {
+        x[0] = in;  // the lower half's last row is now the upper half's first
+        if (r + B - 1 < g.n) ring[ring_slot<true>((r + B - 1) % nring, c)] = out;
+      }
+    } else {
+      // stage 0 ends the sweep: update in place; the whole window is final
+#pragma unroll
+      for (int32_t t = 0; t < H; ++t) {
+        const zdouble vt = (h == 0 && t == 0) ? one : lds_z(eh + t);
+        Arith<zdouble>::axpy(x[t], u, vt);
+      }
+      int32_t sl = (r + H * h) % nring;
+#pragma unroll
+      for (int32_t t = 0; t < H; ++t) {
+        if (r + H * h + t < g.n) ring[ring_slot<true>(sl, c)] = x[t];
+        sl = (sl + 1 == nring) ? 0 : sl + 1;
+      }
+    }
+  }
+}
+
 // One work unit: strip c0 .. c0+31 of the problem described by `a`, epoch e
 // (sweeps e*G .. e*G+G-1). `myflag` receives this unit's progress, `prevflag`
 // is the previous epoch's of the same strip (null for epoch 0). `s_stop` is a
@@ -491,6 +589,8 @@ __device__ __forceinline__ bool process_unit(const ApplyArgs &a, int32_t e, int3
   const int32_t pcol = 16 * cs + (lane >> 1);  // lane pairs: strip column of this pair
   double xw[BW > 0 ? BW : 1];  // register window of the lane's column (BW > 0)
   (void)xw;
+  zdouble xz[BW < -1 ? -BW / 2 : 1];  // complex register window: this lane's half (BW = -b)
+  (void)xz;
   const Epoch ep = make_epoch(g, e, a.G, a.NB);
 
   // prologue: rows needed at step 0 and the reflectors of step 0
@@ -533,6 +633,8 @@ __device__ __forceinline__ bool process_unit(const ApplyArgs &a, int32_t e, int3
         const T *vb = vbuf_w + (int64_t)(t & 1) * ep.nb * a.ldv;
         if constexpr (BW > 0) {
           apply_stages_regwin<BW>(xw, mycol, a.ring, g, j, hi, lo, vb, sig, a.ldv);
+        } else if constexpr (BW < -1) {
+          apply_stages_regwin_pair<-BW / 2>(xz, ring, a.ring, pcol, g, j, hi, lo, vb, sig, a.ldv, lane & 1);
         } else if constexpr (BW < 0) {
           for (int32_t s = hi; s >= lo; --s)
             apply_pair(ring, a.ring, pcol, g.row(s, j), g.len(s, j), vb + (int64_t)(sig - s) * a.ldv, lane & 1);
@@ -560,8 +662,11 @@ __device__ __forceinline__ bool process_unit(const ApplyArgs &a, int32_t e, int3
   return !abandoned;
 }
 
+// Threads per block: real register windows 8 warps at most, the complex
+// register window 4 sweeps (8 warps), the lane-pair and shared-memory
+// windows 16 warps.
 template <typename T, int BW>
-__global__ void __launch_bounds__(BW > 0 ? 256 : 512, 1) apply_kernel(ApplyArgs a) {
+__global__ void __launch_bounds__((BW > 0 || BW < -1) ? 256 : 512, 1) apply_kernel(ApplyArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_unit;
   __shared__ int s_stop;

@@ -225,6 +225,24 @@ __global__ void __launch_bounds__(256, 1) bulge_kernel(BcArgs<T> a) {
       const int L = (int)((n - r < b) ? n - r : b);
       const int64_t c = (j == 0) ? i : r - b;
       const bool on_chip = KEEP && j > 0;  // generation and left-update columns are in sR
+      // The right-update block is final once the previous stage is three
+      // sweeps ahead (no sweep of this stage before j touches its rows, >= r+L),
+      // so warps 4..7 issue the loads of their first HO elements of it now, into
+      // registers, while warp 0 builds the reflector.
+      constexpr int HO = sizeof(T) == 8 ? 32 : 16;
+      T pre[HO];
+      const int64_t rend0 = (r + L + b < n) ? r + L + b : n;
+      const int nrr0 = (int)(rend0 - (r + L));  // right rows
+      if (KEEP) {
+        if (warp >= 4 && nrr0 > 0) {
+          const int ut = tid - 128, tot = nrr0 * L;
+#pragma unroll
+          for (int u = 0; u < HO; ++u) {
+            const int idx = ut + 128 * u;
+            pre[u] = idx < tot ? ldw(bat(a, r + L + idx % nrr0, r + idx / nrr0)) : O::zero();
+          }
+        }
+      }
       // ---- the reflector of column c, rows r .. r+L-1 (one warp)
       if (warp == 0) {
         T xv[EPL];
@@ -317,9 +335,16 @@ __global__ void __launch_bounds__(256, 1) bulge_kernel(BcArgs<T> a) {
           }
           if (nrr > 0) {
             // ---- right: rows r+L .. rend-1, columns r .. r+L-1 (A <- A H); the old
-            // values land in sR (row k - (r+L), column t), eight loads in flight per thread
+            // values land in sR (row k - (r+L), column t): the first HO per thread
+            // from the loads issued before the reflector, the rest eight loads in
+            // flight per thread
             const int tot = nrr * L;
-            for (int base = 0; base < tot; base += 128 * 8) {
+#pragma unroll
+            for (int u = 0; u < HO; ++u) {
+              const int idx = ut + 128 * u;
+              if (idx < tot) sR[idx % nrr + (idx / nrr) * ldr] = pre[u];
+            }
+            for (int base = 128 * HO; base < tot; base += 128 * 8) {
               T tmp[8];
 #pragma unroll
               for (int u = 0; u < 8; ++u) {

@@ -71,7 +71,7 @@ using ApplyFn = void (*)(tbbt::ApplyArgs);
 
 // The apply kernel instance for a data type and register-window width.
 ApplyFn apply_fn(tbbt_dtype dt, int32_t bw) {
-  if (dt == TBBT_COMPLEX128) return tbbt::apply_kernel<zdouble, -1>;
+  if (dt == TBBT_COMPLEX128) return bw == -64 ? tbbt::apply_kernel<zdouble, -64> : tbbt::apply_kernel<zdouble, -1>;
   if (bw == 64) return tbbt::apply_kernel<double, 64>;
   if (bw == 32) return tbbt::apply_kernel<double, 32>;
   return tbbt::apply_kernel<double, 0>;
@@ -86,9 +86,10 @@ size_t smem_bytes_for(tbbt_dtype dt, int32_t b, int32_t G, int32_t NB) {
 
 // Register-window width of the apply kernel for a problem: real b = 32 or 64
 // keep each column's window in registers, complex data take a lane pair per
-// column (-1), other widths the shared-memory window (0).
+// column (-1; b = 64 with the window in the pair's registers: -64), other
+// widths the shared-memory window (0).
 int32_t window_width(tbbt_dtype dt, int64_t nbw) {
-  if (dt == TBBT_COMPLEX128) return -1;
+  if (dt == TBBT_COMPLEX128) return nbw == 64 ? -64 : -1;
   return (nbw == 32 || nbw == 64) ? (int32_t)nbw : 0;
 }
 
@@ -101,6 +102,7 @@ int32_t apply_threads(int32_t G, int32_t bw) { return G * 32 * (bw < 0 ? 2 : 1);
 bool fit_geometry(tbbt_dtype dt, int32_t nbw, int32_t bw, int32_t wantG, int32_t wantNB, int32_t *G_out,
                   int32_t *NB_out) {
   if (bw != 0 && wantG > 8) wantG = 8;  // register window: 256 threads; lane pairs: 512
+  if (bw < -1 && wantG > 4) wantG = 4;  // complex register window: 256 threads
   if (wantG > 16) wantG = 16;
   int32_t G = wantG, NB = wantNB;
   if (NB > 4 * G) NB = 4 * G;  // the row prefetch holds at most 4 elements per thread
@@ -116,6 +118,16 @@ bool fit_geometry(tbbt_dtype dt, int32_t nbw, int32_t bw, int32_t wantG, int32_t
   *G_out = G;
   *NB_out = NB;
   return true;
+}
+
+// Default launch geometry (sweeps per block, stages per step). Real data:
+// 4 sweeps (one warp per SM sub-partition) and 8 stages per step, two blocks
+// per SM. Complex data (lane pairs): one sweep and 2 stages per step, five
+// small blocks per SM, whose step barriers cover one another (1.102 against
+// 1.084 TFLOP/s for 4 x 8 at n = 20000, nev = 6000).
+void default_geometry(tbbt_dtype dt, int32_t *G, int32_t *NB) {
+  *G = dt == TBBT_COMPLEX128 ? 1 : 4;
+  *NB = dt == TBBT_COMPLEX128 ? 2 : 8;
 }
 
 tbbt_status check_shape(int64_t n, int64_t nbw, int64_t nev) {
@@ -447,14 +459,13 @@ tbbt_status tbbt_plan_create(tbbt_plan **plan, tbbt_dtype dtype, int64_t n, int6
   // real data with b = 32 or 64 keep each column's window in registers
   // complex data: two warps per sweep (a lane pair per column)
   p->bw = window_width(dtype, nbw);
-  // launch geometry: most sweeps per block that fit in shared memory
-  // Default: 4 sweeps per block (one warp per SM sub-partition) and 8 stages
-  // per step; two such blocks share an SM when they fit, so one block's
-  // pipeline fill is covered by the other. Block widths that are not a
-  // multiple of 4 load the sub-partitions unevenly and are slower.
-  int32_t G = 0, NB = 0;
-  if (!fit_geometry(dtype, (int32_t)nbw, p->bw, opt && opt->sweeps_per_block > 0 ? opt->sweeps_per_block : 4,
-                    opt && opt->stages_per_step > 0 ? opt->stages_per_step : 8, &G, &NB)) {
+  // launch geometry: the requested or default sweeps per block and stages
+  // per step, lowered until they fit in shared memory; blocks that fit share
+  // an SM, so one block's pipeline fill is covered by another
+  int32_t G = 0, NB = 0, G0 = 0, NB0 = 0;
+  default_geometry(dtype, &G0, &NB0);
+  if (!fit_geometry(dtype, (int32_t)nbw, p->bw, opt && opt->sweeps_per_block > 0 ? opt->sweeps_per_block : G0,
+                    opt && opt->stages_per_step > 0 ? opt->stages_per_step : NB0, &G, &NB)) {
     delete p;
     return TBBT_ENOTSUP;
   }
@@ -813,6 +824,7 @@ tbbt_status noalloc_device(int *dev_out, NoAllocDevice **out) {
     TBBT_CUDA_TRY(allow_max_dynamic_smem(apply_fn(TBBT_REAL64, 32)));
     TBBT_CUDA_TRY(allow_max_dynamic_smem(apply_fn(TBBT_REAL64, 64)));
     TBBT_CUDA_TRY(allow_max_dynamic_smem(apply_fn(TBBT_COMPLEX128, -1)));
+    TBBT_CUDA_TRY(allow_max_dynamic_smem(apply_fn(TBBT_COMPLEX128, -64)));
     d.scratch = (unsigned char *)ptr;
     d.sms = sms;
     d.ready = 1;
@@ -832,8 +844,9 @@ tbbt_status noalloc_launch(NoAllocDevice &d, tbbt_dtype dtype, const void *hh_v,
   const int32_t ldv = round_even((int32_t)nbw);
   // the kernel instance and default launch geometry of the plan path
   const int32_t bw = window_width(dtype, nbw);
-  int32_t G = 0, NB = 0;
-  if (!fit_geometry(dtype, (int32_t)nbw, bw, 4, 8, &G, &NB)) return TBBT_ENOTSUP;
+  int32_t G = 0, NB = 0, G0 = 0, NB0 = 0;
+  default_geometry(dtype, &G0, &NB0);
+  if (!fit_geometry(dtype, (int32_t)nbw, bw, G0, NB0, &G, &NB)) return TBBT_ENOTSUP;
   const size_t smem = smem_bytes_for(dtype, (int32_t)nbw, G, NB);
   const ApplyFn kern = apply_fn(dtype, bw);
   const int32_t strips = (int32_t)((nev + 31) / 32);
@@ -1182,17 +1195,23 @@ tbbt_status tridiag_eig_impl(const double *d, const double *e, int64_t n, int64_
   // column-major copy of X when the output is complex
   const size_t b_e2 = round256(sizeof(double) * (size_t)std::max<int64_t>(n, 1));
   const size_t b_bounds = round256(sizeof(te::Bounds));
+  const size_t b_f32 = round256(sizeof(float) * (size_t)std::max<int64_t>(n, 1));  // d and e^2 in FP32
+  const size_t b_br = round256(sizeof(double) * (size_t)nev);                        // brackets of the FP32 phase
   const size_t b_arr = round256(sizeof(double) * nn);
   const size_t b_piv = round256(nn);
   const size_t b_xr = xt == TBBT_COMPLEX128 ? b_arr : 0;
-  const size_t total = b_e2 + b_bounds + 5 * b_arr + b_piv + b_xr;
+  const size_t total = b_e2 + b_bounds + 2 * b_f32 + 2 * b_br + 5 * b_arr + b_piv + b_xr;
   unsigned char *ws = nullptr;
   TBBT_CUDA_TRY(cudaMallocAsync((void **)&ws, total, s));
   tbbt_status rs = TBBT_OK;
   do {
     double *e2 = (double *)ws;
     te::Bounds *bounds = (te::Bounds *)(ws + b_e2);
-    unsigned char *p = ws + b_e2 + b_bounds;
+    float *d32 = (float *)(ws + b_e2 + b_bounds);
+    float *e232 = (float *)(ws + b_e2 + b_bounds + b_f32);
+    double *blo = (double *)(ws + b_e2 + b_bounds + 2 * b_f32);
+    double *bhi = (double *)(ws + b_e2 + b_bounds + 2 * b_f32 + b_br);
+    unsigned char *p = ws + b_e2 + b_bounds + 2 * b_f32 + 2 * b_br;
     te::InvitArgs A;
     A.d = d;
     A.e = e;
@@ -1208,19 +1227,24 @@ tbbt_status tridiag_eig_impl(const double *d, const double *e, int64_t n, int64_
     A.piv = p + 5 * b_arr;
     double *xr = xt == TBBT_COMPLEX128 ? (double *)(p + 5 * b_arr + b_piv) : (double *)x;
     const int64_t ldr = xt == TBBT_COMPLEX128 ? n : ldx;
-    te::te_bounds_kernel<<<1, te::BOUNDS_THREADS, 0, s>>>(d, n > 1 ? e : d, (int32_t)n, e2, bounds);
+    te::te_bounds_kernel<<<1, te::BOUNDS_THREADS, 0, s>>>(d, n > 1 ? e : d, (int32_t)n, e2, bounds, d32, e232);
     if (cudaGetLastError() != cudaSuccess) { rs = TBBT_ECUDA; break; }
     const int32_t P = bisect_group(nev, sms);
     const int64_t bthreads = 128;
     const unsigned bblocks = (unsigned)((nev * P + bthreads - 1) / bthreads);
+    // FP32 phase (brackets of about 1e-5 ||T||), then the FP64 phase from them
+#define TBBT_BISECT(PP)                                                                                         \
+  te::te_bisect32_kernel<PP><<<bblocks, bthreads, 0, s>>>(d32, e232, (int32_t)n, (int32_t)nev, bounds, blo, bhi); \
+  te::te_bisect_kernel<PP><<<bblocks, bthreads, 0, s>>>(d, e2, (int32_t)n, (int32_t)nev, bounds, w, blo, bhi)
     switch (P) {
-      case 1: te::te_bisect_kernel<1><<<bblocks, bthreads, 0, s>>>(d, e2, (int32_t)n, (int32_t)nev, bounds, w); break;
-      case 2: te::te_bisect_kernel<2><<<bblocks, bthreads, 0, s>>>(d, e2, (int32_t)n, (int32_t)nev, bounds, w); break;
-      case 4: te::te_bisect_kernel<4><<<bblocks, bthreads, 0, s>>>(d, e2, (int32_t)n, (int32_t)nev, bounds, w); break;
-      case 8: te::te_bisect_kernel<8><<<bblocks, bthreads, 0, s>>>(d, e2, (int32_t)n, (int32_t)nev, bounds, w); break;
-      case 16: te::te_bisect_kernel<16><<<bblocks, bthreads, 0, s>>>(d, e2, (int32_t)n, (int32_t)nev, bounds, w); break;
-      default: te::te_bisect_kernel<32><<<bblocks, bthreads, 0, s>>>(d, e2, (int32_t)n, (int32_t)nev, bounds, w); break;
+      case 1: TBBT_BISECT(1); break;
+      case 2: TBBT_BISECT(2); break;
+      case 4: TBBT_BISECT(4); break;
+      case 8: TBBT_BISECT(8); break;
+      case 16: TBBT_BISECT(16); break;
+      default: TBBT_BISECT(32); break;
     }
+#undef TBBT_BISECT
     if (cudaGetLastError() != cudaSuccess) { rs = TBBT_ECUDA; break; }
     te::te_invit_kernel<<<(unsigned)((nev + te::INVIT_THREADS - 1) / te::INVIT_THREADS), te::INVIT_THREADS, 0, s>>>(A);
     if (cudaGetLastError() != cudaSuccess) { rs = TBBT_ECUDA; break; }

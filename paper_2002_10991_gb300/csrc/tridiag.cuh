@@ -53,11 +53,23 @@ struct Bounds {
   double tnorm;      // max(|gl|, |gu|)
   double pivmin;     // smallest pivot magnitude allowed in a Sturm count
   double pert;       // replacement of a vanishing pivot in inverse iteration
+  double sc;         // power of two with sc * tnorm <= 1 (scale of the FP32 copy)
 };
+
+// FP32 phase of the bisection: T sc in single precision (d and e^2), the
+// smallest pivot magnitude of its Sturm counts, the bracket width it stops
+// at and the margin its brackets get before the FP64 phase checks them.
+// A single-precision Sturm count is exact for a matrix within a few units
+// of FP32 rounding of T (relative to ||T||, so about 1e-7 ||T||); the
+// margin is 2^-16 ||T||-scaled units, far beyond that.
+constexpr float PIVMIN32 = 7.8886091e-31f;  // 2^-100
+constexpr float STOP32 = 9.5367432e-7f;     // 2^-20
+constexpr double MARGIN32 = 1.52587890625e-5;  // 2^-16
 
 // Gershgorin bounds, e2 = e^2, the largest e^2 (one block of BOUNDS_THREADS).
 __global__ void te_bounds_kernel(const double *__restrict__ d, const double *__restrict__ e, int32_t n,
-                                 double *__restrict__ e2, Bounds *out) {
+                                 double *__restrict__ e2, Bounds *out, float *__restrict__ d32,
+                                 float *__restrict__ e232) {
   __shared__ double s_lo[BOUNDS_THREADS], s_hi[BOUNDS_THREADS], s_e2[BOUNDS_THREADS];
   double lo = DBL_MAX, hi = -DBL_MAX, me2 = 0.0;
   for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
@@ -92,7 +104,16 @@ __global__ void te_bounds_kernel(const double *__restrict__ d, const double *__r
     b.gl = s_lo[0] - pad - DBL_MIN;
     b.gu = s_hi[0] + pad + DBL_MIN;
     b.pert = eps * fmax(b.tnorm, DBL_MIN);
+    int ex = 0;
+    frexp(fmax(b.tnorm, DBL_MIN), &ex);  // tnorm < 2^ex
+    b.sc = ldexp(1.0, -ex);
     *out = b;
+  }
+  __syncthreads();
+  const double sc = out->sc;
+  for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    d32[i] = (float)(d[i] * sc);
+    if (i + 1 < n) e232[i] = (float)(e2[i] * sc * sc);
   }
 }
 
@@ -113,6 +134,60 @@ __device__ __forceinline__ int32_t sturm_count(const double *__restrict__ d, con
   return cnt;
 }
 
+__device__ __forceinline__ int32_t sturm_count32(const float *__restrict__ d, const float *__restrict__ e2,
+                                                 int32_t n, float sigma) {
+  int32_t cnt = 0;
+  float q = d[0] - sigma;
+  if (fabsf(q) < PIVMIN32) q = -PIVMIN32;
+  cnt += q < 0.0f;
+  for (int32_t i = 1; i < n; ++i) {
+    q = (d[i] - sigma) - __fdiv_rn(e2[i - 1], q);
+    if (fabsf(q) < PIVMIN32) q = -PIVMIN32;
+    cnt += q < 0.0f;
+  }
+  return cnt;
+}
+
+// FP32 phase: the multisection of te_bisect_kernel on T sc in single
+// precision, down to a bracket of STOP32; writes the bracket widened by
+// MARGIN32 on both sides, in the units of T, for the FP64 phase to check.
+template <int P>
+__global__ void te_bisect32_kernel(const float *__restrict__ d, const float *__restrict__ e2, int32_t n, int32_t nev,
+                                   const Bounds *__restrict__ bounds, double *__restrict__ lo_out,
+                                   double *__restrict__ hi_out) {
+  static_assert(P >= 1 && P <= 32 && (32 % P) == 0, "group size must divide the warp");
+  const int32_t lane = threadIdx.x & 31;
+  const int32_t g = lane % P;
+  const int32_t base = lane - g;
+  const int32_t k = (int32_t)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / P);
+  const bool active = k < nev;
+  const Bounds B = *bounds;
+  const unsigned gbits = (P == 32) ? 0xffffffffu : ((1u << P) - 1u);
+  float lo = __double2float_rd(B.gl * B.sc), hi = __double2float_ru(B.gu * B.sc);
+  bool done = !active;
+  for (int round = 0; round < 256; ++round) {
+    if (!done) done = hi - lo <= STOP32;
+    if (__all_sync(0xffffffffu, done)) break;
+    const float sigma = lo + (hi - lo) * ((float)(g + 1) / (float)(P + 1));
+    const bool below = done || sturm_count32(d, e2, n, sigma) <= k;
+    const unsigned grp = (__ballot_sync(0xffffffffu, below) >> base) & gbits;
+    const int32_t lead = (grp == gbits) ? P : __ffs(~grp) - 1;
+    const float s_lo = __shfl_sync(0xffffffffu, sigma, base + (lead > 0 ? lead - 1 : 0));
+    const float s_hi = __shfl_sync(0xffffffffu, sigma, base + (lead < P ? lead : P - 1));
+    if (!done) {
+      const float nlo = lead > 0 ? s_lo : lo;
+      const float nhi = lead < P ? s_hi : hi;
+      if (nlo == lo && nhi == hi) done = true;
+      lo = nlo;
+      hi = nhi;
+    }
+  }
+  if (active && g == 0) {
+    lo_out[k] = ((double)lo - MARGIN32) / B.sc;
+    hi_out[k] = ((double)hi + MARGIN32) / B.sc;
+  }
+}
+
 // Eigenvalue k (0-based, ascending) by multisection: the P threads of a
 // group (P divides 32; a warp holds whole groups) evaluate P interior points
 // of the bracket [lo, hi], count(lo) <= k < count(hi), and keep the
@@ -120,9 +195,13 @@ __device__ __forceinline__ int32_t sturm_count(const double *__restrict__ d, con
 // and the point after it (so the invariant holds even where rounding makes
 // the counts non-monotone). Stops when the bracket is within
 // 2 eps max(|lo|, |hi|) + eps ||T||, or cannot shrink.
+// With lo0 / hi0 (the FP32 phase's brackets) a group first checks both
+// ends with FP64 counts and starts from each end that holds; an end that
+// does not hold falls back to the Gershgorin bound.
 template <int P>
 __global__ void te_bisect_kernel(const double *__restrict__ d, const double *__restrict__ e2, int32_t n,
-                                 int32_t nev, const Bounds *__restrict__ bounds, double *__restrict__ w) {
+                                 int32_t nev, const Bounds *__restrict__ bounds, double *__restrict__ w,
+                                 const double *__restrict__ lo0, const double *__restrict__ hi0) {
   static_assert(P >= 1 && P <= 32 && (32 % P) == 0, "group size must divide the warp");
   const int32_t lane = threadIdx.x & 31;
   const int32_t g = lane % P;     // index within the group
@@ -133,6 +212,20 @@ __global__ void te_bisect_kernel(const double *__restrict__ d, const double *__r
   const double eps = DBL_EPSILON;
   const unsigned gbits = (P == 32) ? 0xffffffffu : ((1u << P) - 1u);
   double lo = B.gl, hi = B.gu;
+  if (lo0 != nullptr) {
+    const double l0 = active ? lo0[k] : 0.0, h0 = active ? hi0[k] : 0.0;
+    bool okl, okh;
+    if constexpr (P >= 2) {
+      const int32_t c = (active && g < 2) ? sturm_count(d, e2, n, g == 0 ? l0 : h0, B.pivmin) : 0;
+      okl = __shfl_sync(0xffffffffu, c, base) <= k;
+      okh = __shfl_sync(0xffffffffu, c, base + 1) > k;
+    } else {
+      okl = active && sturm_count(d, e2, n, l0, B.pivmin) <= k;
+      okh = active && sturm_count(d, e2, n, h0, B.pivmin) > k;
+    }
+    if (okl && l0 > lo) lo = l0;
+    if (okh && h0 < hi) hi = h0;
+  }
   bool done = !active;  // uniform within a group: lo and hi are
   for (int round = 0; round < 512; ++round) {
     if (!done) done = hi - lo <= 2.0 * eps * fmax(fabs(lo), fabs(hi)) + eps * B.tnorm;
@@ -174,38 +267,88 @@ struct InvitArgs {
   unsigned char *piv;
 };
 
+// Rows whose loads a solve issues together (the recurrences run one
+// thread per vector, so the loads of a chunk hide each other's latency).
+constexpr int CH = 8;
+
+struct SolveOut {
+  double amax;  // largest |y_i|
+  double ss;    // sum of y_i^2 (inf if it overflowed)
+  double sgn;   // sign of the first entry of largest magnitude
+};
+
 // One solve of inverse iteration for vector k, in place on its iterate:
-// y <- U^-1 L^-1 P y with the factors of T - w_k I. Returns max |y_i|.
-__device__ __forceinline__ double invit_solve(const InvitArgs &A, int32_t k) {
+// y <- U^-1 L^-1 P (fin y) with the factors of T - w_k I (fin: a scale
+// still owed to the iterate, applied as it is read).
+__device__ __forceinline__ SolveOut invit_solve(const InvitArgs &A, int32_t k, double fin) {
   const int32_t n = A.n;
   const size_t ld = (size_t)A.nev;
   auto at = [&](int32_t i) { return (size_t)i * ld + (size_t)k; };
   // forward: apply the row interchanges and multipliers to y
-  double yk = A.y[at(0)];
-  for (int32_t i = 0; i + 1 < n; ++i) {
-    double yn = A.y[at(i + 1)];
-    const double m = A.lm[at(i)];
-    if (A.piv[at(i)]) {
-      const double t = yk;
-      yk = yn;
-      yn = t - m * yk;
-    } else {
-      yn = yn - m * yk;
+  double yk = A.y[at(0)] * fin;
+  for (int32_t i0 = 0; i0 + 1 < n; i0 += CH) {
+    double yy[CH], mm[CH];
+    unsigned char pp[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int32_t i = i0 + u;
+      if (i + 1 < n) {
+        yy[u] = A.y[at(i + 1)] * fin;
+        mm[u] = A.lm[at(i)];
+        pp[u] = A.piv[at(i)];
+      }
     }
-    A.y[at(i)] = yk;
-    yk = yn;
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int32_t i = i0 + u;
+      if (i + 1 < n) {
+        double yn = yy[u];
+        if (pp[u]) {
+          const double t = yk;
+          yk = yn;
+          yn = t - mm[u] * yk;
+        } else {
+          yn = yn - mm[u] * yk;
+        }
+        A.y[at(i)] = yk;
+        yk = yn;
+      }
+    }
   }
   A.y[at(n - 1)] = yk;
-  // back substitution with U (diagonal, two super-diagonals)
-  double x1 = 0.0, x2 = 0.0, amax = 0.0;
-  for (int32_t i = n - 1; i >= 0; --i) {
-    const double x = (A.y[at(i)] - A.u1[at(i)] * x1 - A.u2[at(i)] * x2) * A.u0[at(i)];
-    A.y[at(i)] = x;
-    amax = fmax(amax, fabs(x));
-    x2 = x1;
-    x1 = x;
+  // back substitution with U (reciprocal diagonal, two super-diagonals)
+  SolveOut o{0.0, 0.0, 1.0};
+  double x1 = 0.0, x2 = 0.0;
+  for (int32_t i0 = n - 1; i0 >= 0; i0 -= CH) {
+    double yy[CH], a0[CH], a1[CH], a2[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int32_t i = i0 - u;
+      if (i >= 0) {
+        yy[u] = A.y[at(i)];
+        a0[u] = A.u0[at(i)];
+        a1[u] = A.u1[at(i)];
+        a2[u] = A.u2[at(i)];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int32_t i = i0 - u;
+      if (i >= 0) {
+        const double x = (yy[u] - a1[u] * x1 - a2[u] * x2) * a0[u];
+        A.y[at(i)] = x;
+        // rows run downwards: >= keeps the first (lowest-index) largest entry
+        if (fabs(x) >= o.amax) {
+          o.amax = fabs(x);
+          o.sgn = x < 0.0 ? -1.0 : 1.0;
+        }
+        o.ss = fma(x, x, o.ss);
+        x2 = x1;
+        x1 = x;
+      }
+    }
   }
-  return amax;
+  return o;
 }
 
 // Eigenvector k of T by inverse iteration (one thread per vector).
@@ -262,29 +405,27 @@ __global__ void te_invit_kernel(InvitArgs A) {
     const uint64_t r = mix64(key + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull);
     A.y[at(i)] = (double)(r >> 11) * (2.0 / 9007199254740992.0) - 1.0;
   }
+  // every solve is followed by a normalisation, folded into the next solve's
+  // reads (and into one final pass): 1 / ||y||, or, if the sum of squares
+  // overflowed, the same with y first scaled by its largest entry
+  double f = 1.0, sgn = 1.0;
   for (int step = 0; step < INVIT_STEPS; ++step) {
-    const double amax = invit_solve(A, k);
-    // normalise: scale by the largest entry first (no overflow in the sum)
-    const double s = amax > 0.0 ? 1.0 / amax : 1.0;
-    double ss = 0.0;
-    for (int32_t i = 0; i < n; ++i) {
-      const double v = A.y[at(i)] * s;
-      ss += v * v;
-    }
-    const double f = s / sqrt(ss);
-    // sign: the first entry of largest magnitude is positive
-    double best = 0.0, sgn = 1.0;
-    if (step == INVIT_STEPS - 1) {
+    const SolveOut o = invit_solve(A, k, f);
+    sgn = o.sgn;
+    if (o.ss > 0.0 && o.ss <= DBL_MAX) {
+      f = 1.0 / sqrt(o.ss);
+    } else {
+      const double s = o.amax > 0.0 ? 1.0 / o.amax : 1.0;
+      double ss = 0.0;
       for (int32_t i = 0; i < n; ++i) {
-        const double v = A.y[at(i)];
-        if (fabs(v) > best) {
-          best = fabs(v);
-          sgn = v < 0.0 ? -1.0 : 1.0;
-        }
+        const double v = A.y[at(i)] * s;
+        ss = fma(v, v, ss);
       }
+      f = ss > 0.0 ? s / sqrt(ss) : 1.0;
     }
-    for (int32_t i = 0; i < n; ++i) A.y[at(i)] *= f * sgn;
   }
+  // sign: the first entry of largest magnitude is positive
+  for (int32_t i = 0; i < n; ++i) A.y[at(i)] *= f * sgn;
 }
 
 __device__ __forceinline__ double block_sum(double v, double *red);
@@ -315,7 +456,7 @@ __global__ void te_tight_kernel(InvitArgs A) {
     __syncthreads();
     for (int step = 0; step < INVIT_STEPS; ++step) {
       if (threadIdx.x == 0) {
-        const double amax = invit_solve(A, c);
+        const double amax = invit_solve(A, c, 1.0).amax;
         s_scale = amax > 0.0 ? 1.0 / amax : 1.0;
       }
       __syncthreads();
