@@ -490,6 +490,365 @@ __global__ void __launch_bounds__(256, 1) bulge_kernel(BcArgs<T> a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Two-CTA form (the right block kept on chip): a cluster of two CTAs runs one
+// stage. CTA 0 builds each sweep's reflector and applies the left and right
+// updates with all eight warps (four threads per column / row); CTA 1
+// applies the diagonal-block update D <- H^H D H with all eight warps. A
+// sweep's FP64 work is thus split over two SMs, and the two halves run side
+// by side:
+//  * CTA 0 claims the stage and passes its index to CTA 1 (a store into CTA
+//    1's shared memory and an arrival on its `stage` barrier);
+//  * both wait for the previous stage's progress (the lag rule above);
+//  * CTA 0's warp 0 writes the reflector and tau into CTA 1's shared memory
+//    and arrives on its `refl` barrier (one arrival per lane, after the
+//    lane's stores);
+//  * CTA 1 loads D (it may run ahead: D of sweep j+1 shares no entry with
+//    sweep j's updates), waits for the reflector, updates D, stores it to L2,
+//    fences at GPU scope and arrives on CTA 0's `diag` barrier;
+//  * CTA 0, after its own updates, waits for `diag` before it publishes the
+//    sweep's progress.
+// Every wait is bounded and also gives up when the device error word is set.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_cluster(uint32_t addr, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;\n" ::"r"(addr), "d"(v) : "memory");
+}
+__device__ __forceinline__ void st_cluster(uint32_t addr, zdouble v) {
+  asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};\n" ::"r"(addr), "d"(v.re), "d"(v.im) : "memory");
+}
+__device__ __forceinline__ void st_cluster_i32(uint32_t addr, int v) {
+  asm volatile("st.shared::cluster.b32 [%0], %1;\n" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void bc_mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// arrival on a barrier in the peer CTA's shared memory (release at cluster scope)
+__device__ __forceinline__ void bc_arrive_remote(uint32_t remote_bar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];\n" ::"r"(remote_bar) : "memory");
+}
+__device__ __forceinline__ bool bc_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of the given parity (0: done; 1: gave up).
+__device__ inline int bc_wait(uint64_t *bar, uint32_t parity, int *err, long long timeout_ns) {
+  if (bc_try_wait(bar, parity)) return 0;
+  const long long t0 = globaltimer_ns();
+  for (unsigned it = 1;; ++it) {
+    if (bc_try_wait(bar, parity)) return 0;
+    if ((it & 15) == 0) {
+      if (*(volatile int *)err != 0) return 1;
+      if (globaltimer_ns() - t0 > timeout_ns) {
+        atomicCAS(err, 0, 4 /* TBBT_ETIMEOUT */);
+        return 1;
+      }
+    }
+  }
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+// Shared memory of the two-CTA form, in elements of T: the reflector, then
+// (CTA 0) the right block padded to b+1 rows and four partial dot products
+// per column / row, or (CTA 1) the diagonal block, y and eight partial sums.
+__host__ __device__ constexpr int64_t bc2_smem_elems(int b) {
+  return (int64_t)kBcMaxB + (((int64_t)b * (b + 1) + 4 * kBcMaxB) > ((int64_t)b * b + 9 * kBcMaxB)
+                                 ? ((int64_t)b * (b + 1) + 4 * kBcMaxB)
+                                 : ((int64_t)b * b + 9 * kBcMaxB));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 1) bulge_cluster_kernel(BcArgs<T> a) {
+  using O = Ops<T>;
+  constexpr int EPL = kBcMaxB / 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = a.g.b;
+  T *sv = reinterpret_cast<T *>(smem_raw);  // reflector (both CTAs: CTA 0 writes CTA 1's copy)
+  // CTA 0
+  T *sR = sv + kBcMaxB;                     // right block: sR[t + s ldr] = A[r + t, c + s] of the next sweep
+  const int ldr = b + 1;
+  T *sPart = sR + (int64_t)b * ldr;         // four partial dot products per column / row
+  // CTA 1
+  T *sD = sv + kBcMaxB;                     // diagonal block, b x b (column-major, ld b)
+  T *sy = sD + (int64_t)b * b;              // y = D v
+  T *sy8 = sy + kBcMaxB;                    // eight partial sums of y
+  __shared__ __align__(8) uint64_t bar_stage, bar_refl, bar_diag;
+  __shared__ T s_tau;
+  __shared__ int s_stage;
+  __shared__ int s_stop;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t rank = cluster_ctarank();
+  const int32_t n = a.g.n;
+  if (tid == 0) {
+    bc_mbar_init(&bar_stage, 1);  // CTA 1: the stage index arrived
+    bc_mbar_init(&bar_refl, 32);  // CTA 1: the reflector arrived (one arrival per lane of CTA 0's warp 0)
+    bc_mbar_init(&bar_diag, 1);   // CTA 0: CTA 1 stored the sweep's diagonal block
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  cluster_sync_all();  // the peer's barriers exist before anyone arrives on them
+  const uint32_t peer = rank ^ 1u;
+  const uint32_t r_stage = mapa_shared(smem_u32(&s_stage), peer);
+  const uint32_t r_tau = mapa_shared(smem_u32(&s_tau), peer);
+  const uint32_t r_sv = mapa_shared(smem_u32(sv), peer);
+  const uint32_t r_bar_stage = mapa_shared(smem_u32(&bar_stage), peer);
+  const uint32_t r_bar_refl = mapa_shared(smem_u32(&bar_refl), peer);
+  const uint32_t r_bar_diag = mapa_shared(smem_u32(&bar_diag), peer);
+  uint32_t n_stage = 0, n_sweep = 0;  // completed phases of the stage and per-sweep barriers
+  for (;;) {
+    // ---- the stage: CTA 0 claims it and passes it on
+    if (tid == 0) {
+      if (rank == 0) {
+        const int st = (int)atomicAdd(a.counter, 1u);
+        s_stage = st;
+        s_stop = (*(volatile int *)a.err != 0);
+        st_cluster_i32(r_stage, st);
+        bc_arrive_remote(r_bar_stage);
+      } else {
+        s_stop = bc_wait(&bar_stage, n_stage & 1, a.err, a.timeout_ns);
+      }
+    }
+    ++n_stage;
+    __syncthreads();
+    const int i = s_stage;
+    if (s_stop || i >= a.nstages) break;
+    const int32_t nsweep = (i <= n - 3) ? (n - i - 2 + b - 1) / b : 1;
+    const int32_t prev_sweeps = (i >= 1) ? ((i - 1 <= n - 3) ? (n - i - 1 + b - 1) / b : 1) : 0;
+    int *mine = a.progress + i;
+    bool abandoned = false;
+    for (int32_t j = 0; j < nsweep; ++j, ++n_sweep) {
+      if (tid == 0 && i >= 1) s_stop = wait_progress(a.err, a.timeout_ns, a.progress + i - 1, min(j + 3, prev_sweeps));
+      __syncthreads();
+      if (s_stop) {
+        abandoned = true;
+        break;
+      }
+      const int64_t r = i + 1 + (int64_t)j * b;
+      const int L = (int)((n - r < b) ? n - r : b);
+      const int64_t c = (j == 0) ? i : r - b;
+      const bool on_chip = j > 0;
+      if (rank == 0) {
+        // ---- right block: the first HO elements of each thread, loaded now
+        constexpr int HO = 16;
+        T pre[HO];
+        const int64_t rend = (r + L + b < n) ? r + L + b : n;
+        const int nrr = (int)(rend - (r + L));
+        const int tot = nrr * L;
+#pragma unroll
+        for (int u = 0; u < HO; ++u) {
+          const int idx = tid + 256 * u;
+          pre[u] = idx < tot ? ldw(bat(a, r + L + idx % nrr, r + idx / nrr)) : O::zero();
+        }
+        // ---- the reflector of column c (warp 0), also into CTA 1
+        if (warp == 0) {
+          T xv[EPL];
+          double s2 = 0.0;
+#pragma unroll
+          for (int e = 0; e < EPL; ++e) {
+            const int t = lane + 32 * e;
+            xv[e] = (t < L) ? (on_chip ? sR[t] : ldw(bat(a, r + t, c))) : O::zero();
+            if (t >= 1) {
+              s2 = fma(O::re(xv[e]), O::re(xv[e]), s2);
+              s2 = fma(O::im(xv[e]), O::im(xv[e]), s2);
+            }
+          }
+#pragma unroll
+          for (int o = 16; o; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+          const double ar = __shfl_sync(0xffffffffu, O::re(xv[0]), 0);
+          const double ai = __shfl_sync(0xffffffffu, O::im(xv[0]), 0);
+          T tau, scal;
+          double beta;
+          if (s2 == 0.0 && ai == 0.0) {
+            tau = O::zero();
+            beta = ar;
+            scal = O::zero();
+          } else {
+            const double nrm = sqrt(ar * ar + ai * ai + s2);
+            beta = ar >= 0.0 ? -nrm : nrm;
+            tau = O::make((beta - ar) / beta, -ai / beta);
+            const double dr = ar - beta, di = ai;
+            const double den = dr * dr + di * di;
+            scal = O::make(dr / den, -di / den);
+          }
+          const bool zs = O::re(scal) == 0.0 && O::im(scal) == 0.0;
+#pragma unroll
+          for (int e = 0; e < EPL; ++e) {
+            const int t = lane + 32 * e;
+            if (t < L) {
+              const T vt = (t == 0) ? O::make(1.0, 0.0) : (zs ? O::zero() : O::mul(xv[e], scal));
+              sv[t] = vt;
+              st_cluster(r_sv + (uint32_t)(t * sizeof(T)), vt);
+              const T piv = (t == 0) ? O::make(beta, 0.0) : O::zero();
+              if (on_chip)
+                sR[t] = piv;
+              else
+                stw(bat(a, r + t, c), piv);
+            }
+          }
+          if (lane == 0) {
+            s_tau = tau;
+            st_cluster(r_tau, tau);
+          }
+          bc_arrive_remote(r_bar_refl);  // after this lane's stores into CTA 1
+          const int64_t k = a.stage_off[i] + j;
+          __syncwarp();
+          for (int t = lane; t < b; t += 32) a.hh_v[k * b + t] = (t < L) ? sv[t] : O::zero();
+          if (lane == 0) a.hh_tau[k] = tau;
+        }
+        __syncthreads();
+        const T tau = s_tau;
+        const T ctau = O::conj(tau);
+        const int q = tid % 64, h = tid / 64;  // four threads per column / row
+        const int tlo = (L * h) / 4, thi = (L * (h + 1)) / 4;
+        if (on_chip) {
+          // ---- left, on chip: columns c+1 .. r-1 are sR columns 1 .. b-1
+          for (int sc = 1 + q; sc < b; sc += 64) {
+            const T *col = sR + (int64_t)sc * ldr;
+            T wsum = O::zero();
+            for (int t = tlo; t < thi; ++t) wsum = O::fma_(O::conj(sv[t]), col[t], wsum);
+            sPart[h * kBcMaxB + sc] = wsum;
+          }
+          __syncthreads();
+          for (int sc = 1 + q; sc < b; sc += 64) {
+            T *col = sR + (int64_t)sc * ldr;
+            const T f = O::mul(ctau, add(add(sPart[sc], sPart[kBcMaxB + sc]),
+                                         add(sPart[2 * kBcMaxB + sc], sPart[3 * kBcMaxB + sc])));
+            for (int t = tlo; t < thi; ++t) col[t] = O::fms_(f, sv[t], col[t]);
+          }
+          __syncthreads();
+          for (int idx = tid; idx < L * b; idx += 256) {
+            const int t = idx % L, sc = idx / L;
+            stw(bat(a, r + t, c + sc), sR[t + sc * ldr]);
+          }
+          __syncthreads();  // every read of sR done before the right update refills it
+        }
+        if (nrr > 0) {
+          // ---- right: rows r+L .. rend-1, columns r .. r+L-1 (A <- A H)
+#pragma unroll
+          for (int u = 0; u < HO; ++u) {
+            const int idx = tid + 256 * u;
+            if (idx < tot) sR[idx % nrr + (idx / nrr) * ldr] = pre[u];
+          }
+          for (int base = 256 * HO; base < tot; base += 256 * 8) {
+            T tmp[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int idx = base + tid + 256 * u;
+              tmp[u] = idx < tot ? ldw(bat(a, r + L + idx % nrr, r + idx / nrr)) : O::zero();
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int idx = base + tid + 256 * u;
+              if (idx < tot) sR[idx % nrr + (idx / nrr) * ldr] = tmp[u];
+            }
+          }
+          __syncthreads();
+          for (int kk = q; kk < nrr; kk += 64) {
+            T wsum = O::zero();
+            for (int t = tlo; t < thi; ++t) wsum = O::fma_(sR[kk + t * ldr], sv[t], wsum);
+            sPart[h * kBcMaxB + kk] = wsum;
+          }
+          __syncthreads();
+          for (int kk = q; kk < nrr; kk += 64) {
+            const T f = O::mul(tau, add(add(sPart[kk], sPart[kBcMaxB + kk]),
+                                        add(sPart[2 * kBcMaxB + kk], sPart[3 * kBcMaxB + kk])));
+            for (int t = tlo; t < thi; ++t) sR[kk + t * ldr] = O::fms_(f, O::conj(sv[t]), sR[kk + t * ldr]);
+          }
+          if (j + 1 == nsweep) {
+            __syncthreads();
+            for (int idx = tid; idx < tot; idx += 256)
+              stw(bat(a, r + L + idx % nrr, r + idx / nrr), sR[idx % nrr + (idx / nrr) * ldr]);
+          }
+        }
+        __syncthreads();
+        // CTA 1's diagonal block of this sweep is in L2 before the progress release
+        if (tid == 0) s_stop = bc_wait(&bar_diag, n_sweep & 1, a.err, a.timeout_ns);
+        __syncthreads();
+        if (s_stop) {
+          abandoned = true;
+          break;
+        }
+        if (tid == 0) st_release(mine, j + 1);
+      } else {
+        // ---- CTA 1: the diagonal block, D <- H^H D H = D - w v^H - v w^H
+        for (int idx = tid; idx < L * L; idx += 256) {
+          const int t = idx % L, s2 = idx / L;
+          sD[t + s2 * b] = hget(a, r + t, r + s2);
+        }
+        if (tid == 0) s_stop = bc_wait(&bar_refl, n_sweep & 1, a.err, a.timeout_ns);
+        __syncthreads();
+        if (s_stop) {
+          abandoned = true;
+          break;
+        }
+        const T tau = s_tau;
+        {
+          // y = D v: warp w sums the eighth w of the columns, then the eight add up
+          const int q0 = (L * warp) / 8, q1 = (L * (warp + 1)) / 8;
+          for (int t = lane; t < L; t += 32) {
+            T acc = O::zero();
+            for (int s2 = q0; s2 < q1; ++s2) acc = O::fma_(sD[t + s2 * b], sv[s2], acc);
+            sy8[warp * kBcMaxB + t] = acc;
+          }
+        }
+        __syncthreads();
+        for (int t = tid; t < L; t += 256) {
+          T acc = sy8[t];
+#pragma unroll
+          for (int w8 = 1; w8 < 8; ++w8) acc = add(acc, sy8[w8 * kBcMaxB + t]);
+          sy[t] = acc;
+        }
+        __syncthreads();
+        double al = 0.0;  // v^H y (real), every warp reduces it for itself
+        for (int t = lane; t < L; t += 32) al += O::re(O::mul(O::conj(sv[t]), sy[t]));
+#pragma unroll
+        for (int o = 16; o; o >>= 1) al += __shfl_xor_sync(0xffffffffu, al, o);
+        const double tt2 = O::re(tau) * O::re(tau) + O::im(tau) * O::im(tau);
+        const double half = 0.5 * tt2 * al;
+        T *sw = sy8;  // the partial sums are consumed
+        __syncthreads();
+        for (int t = tid; t < L; t += 256) sw[t] = O::fms_(O::make(half, 0.0), sv[t], O::mul(tau, sy[t]));
+        __syncthreads();
+        for (int idx = tid; idx < L * L; idx += 256) {
+          const int t = idx % L, s2 = idx / L;
+          if (t < s2) continue;
+          T dv = sD[t + s2 * b];
+          dv = O::fms_(sw[t], O::conj(sv[s2]), dv);
+          dv = O::fms_(sv[t], O::conj(sw[s2]), dv);
+          if (t == s2) dv = O::make(O::re(dv), 0.0);
+          stw(bat(a, r + t, r + s2), dv);
+        }
+        __syncthreads();
+        if (tid == 0) {
+          __threadfence();  // the stores above are visible GPU-wide before CTA 0 publishes
+          bc_arrive_remote(r_bar_diag);
+        }
+      }
+    }
+    if (abandoned && rank == 0 && tid == 0) st_release(mine, kPoison);
+    __syncthreads();
+    if (abandoned) break;
+  }
+  cluster_sync_all();  // no access to the peer's shared memory after this
+}
+
 // Diagonal and (real) sub-diagonal of the reduced band.
 template <typename T>
 __global__ void bulge_extract_kernel(const T *w, int64_t ldw, int32_t n, double *d, double *e) {

@@ -1008,8 +1008,35 @@ tbbt_status bulge_chase_impl(const T *band, int64_t ldb, int64_t n, int64_t nbw,
       cudaGetSymbolAddress((void **)&err, g_tbbt_error);
       a.err = err;
       a.timeout_ns = 20000000000LL;
-      const int grid = std::min<int32_t>(nstages, sms > 0 ? sms : 1);
-      kern<<<grid, 256, smem, s>>>(a);
+      const size_t smem2 = (size_t)tbbt::bc::bc2_smem_elems((int)nbw) * sizeof(T);
+      if (keep && smem2 <= (size_t)kMaxSmem) {
+        // two-CTA form: clusters of two CTAs, one stage each
+        auto kern2 = tbbt::bc::bulge_cluster_kernel<T>;
+        if (cudaFuncSetAttribute(kern2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2) != cudaSuccess) {
+          rs = TBBT_ECUDA;
+          break;
+        }
+        const int clusters = std::min<int32_t>(nstages, std::max(sms / 2, 1));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(2 * clusters));
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = smem2;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (cudaLaunchKernelEx(&cfg, kern2, a) != cudaSuccess) {
+          rs = TBBT_ECUDA;
+          break;
+        }
+      } else {
+        const int grid = std::min<int32_t>(nstages, sms > 0 ? sms : 1);
+        kern<<<grid, 256, smem, s>>>(a);
+      }
       if (cudaGetLastError() != cudaSuccess) {
         rs = TBBT_ECUDA;
         break;

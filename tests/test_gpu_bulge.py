@@ -41,8 +41,10 @@ def test_bulge_chase_matches_oracle(P, n, b, cplx):
     scale = max(1.0, np.abs(W).max())
     assert np.abs(d_g - d_o).max(initial=0) <= 1e-12 * scale * n
     assert np.abs(e_g - e_o).max(initial=0) <= 1e-12 * scale * n
-    assert np.abs(t_g - t_o).max(initial=0) <= 1e-10
-    assert np.abs(v_g - v_o).max(initial=0) <= 1e-9
+    # measured on GB300: |dtau| <= 5.5e-12, |dv| <= 6.5e-12 over these shapes (n = 513, b = 64 the
+    # largest); the reflectors follow the rounding of the entries they annihilate
+    assert np.abs(t_g - t_o).max(initial=0) <= 5e-11
+    assert np.abs(v_g - v_o).max(initial=0) <= 5e-11
     # the back-transformation of the two stores agrees on a unitary block
     if n >= 3:
         X = I.eigvec_block(n, min(n, 24), 7, cplx)
