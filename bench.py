@@ -132,11 +132,38 @@ def set_workload(name: str):
     WORKLOAD = name
 
 
+def b2f_split_tensor_flops(n: int, b: int, nev: int, sms: int) -> float:
+    """BF16 tensor-core flops of the split band -> full form per call: per
+    128-column strip, per WY block and per 96-row batch of a slot's 32-row
+    tiles, 26 digit-pair products in each contraction (128 x 32 x 96, and
+    three of 128 x 32 x 32). Slots and tiles as the library deals them."""
+    K1 = max(n - b, 0)
+    if K1 == 0 or nev == 0:
+        return 0.0
+    P_, ntiles, strips = (K1 + 31) // 32, (n + 31) // 32, (nev + 127) // 128
+    best, SK = None, 1
+    for sk in range(1, min(8, sms) + 1):
+        conc = max(sms // sk, 1)
+        t = -(-strips // conc) / sk
+        if sk == 1 or t < best * 0.999:
+            best, SK = t, sk
+    batches = 0
+    for p in range(P_):
+        t0 = (32 * p + b) // 32
+        for k in range(SK):
+            f = t0 + ((k - t0) % SK)
+            cnt = (ntiles - 1 - f) // SK + 1 if f < ntiles else 0
+            batches += (cnt + 2) // 3
+    per_batch = 26 * 2.0 * 128 * 32 * 96 * 2
+    return per_batch * batches * strips
+
+
 def b2f_bench(args):
     """Band -> full back-transformation (Eq. 6e) on the GPU: one call of the
     C ABI per step (T factors of the 32-reflector blocks, then the apply
-    kernel), timed with CUDA events on the calling stream; the oracle on the
-    host cores on a column sample; parity on sampled columns."""
+    kernel; the split form adds its digit preparation and the fixed-point
+    conversions), timed with CUDA events on the calling stream; the oracle on
+    the host cores on a column sample; parity on sampled columns."""
     import torch
 
     import oracle
@@ -144,26 +171,29 @@ def b2f_bench(args):
 
     torch.cuda.set_device(0)
     n, b, nev, cplx, seed = B2F_WORKLOADS[WORKLOAD]
+    if args.variant not in ("fp64", "split-tc") or (cplx and args.variant != "fp64"):
+        raise SystemExit("band -> full: --variant fp64, or split-tc for real data")
+    variant = VARIANTS[args.variant]
     a, tau = I.synthetic_full_store(n, b, seed, cplx)
     Y = I.eigvec_block(n, nev, seed + 1, cplx)
     da = torch.from_numpy(np.ascontiguousarray(a.T)).cuda().t()
     dt = torch.from_numpy(tau).cuda()
     dq = torch.from_numpy(np.ascontiguousarray(Y.T)).cuda().t()
     cols = np.unique(np.linspace(0, nev - 1, 8).astype(int))
-    P.trans_ev_band_to_full(da, dt, n, b, nev, dq)  # parity pass on the original columns
+    P.trans_ev_band_to_full(da, dt, n, b, nev, dq, variant=variant)  # parity pass on the original columns
     P.stream_check()
     Cg = dq[:, torch.from_numpy(cols).cuda()].cpu().numpy()
     Co = oracle.back_transform_full(a, tau, n, b, np.asfortranarray(Y[:, cols]), nthreads=oracle.num_cpus())
     err = float(np.abs(Cg - Co).max())
     for _ in range(max(args.warmup, 1)):
-        P.trans_ev_band_to_full(da, dt, n, b, nev, dq)
+        P.trans_ev_band_to_full(da, dt, n, b, nev, dq, variant=variant)
     P.stream_check()
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clocks:
         e0.record(stream)
         for _ in range(args.steps):
-            P.trans_ev_band_to_full(da, dt, n, b, nev, dq)
+            P.trans_ev_band_to_full(da, dt, n, b, nev, dq, variant=variant)
         e1.record(stream)
         torch.cuda.synchronize()
     P.stream_check()
@@ -180,19 +210,30 @@ def b2f_bench(args):
     oracle.back_transform_full(a, tau, n, b, Ys, nthreads=cores)
     cpu_s = time.perf_counter() - t0
     cpu_tf = (16.0 if cplx else 4.0) * ncs * sum_l / cpu_s / 1e12
+    if args.variant == "fp64":
+        roof = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "tbbt::bf::bf_apply_kernel (timed with the T-factor kernel: the whole call)"}
+    else:
+        tens = b2f_split_tensor_flops(n, b, nev, torch.cuda.get_device_properties(0).multi_processor_count)
+        ach = tens / (ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": ach, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / BF16_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS bf16 GEMM burst)",
+                "fp64_equivalent_tflops": tflops, "tensor_flops_per_step": tens,
+                "kernel": "tbbt::bfs::bfs_apply_kernel (timed with the preparation kernels: the whole call)"}
     line = {
         "metric": "band->full back-transform TFLOP/s (Eq. 6e)", "value": tflops, "unit": "TFLOP/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c128" if cplx else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "nbw": b, "nev": nev, "reflectors": K1,
                    "store": "seeded unitary reflectors, LAPACK layout", "l2": "inputs larger than L2"},
-        "roofline": {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": tflops / FP64_PEAK_TFLOPS, "traffic": None,
-                     "kernel": "tbbt::bf::bf_apply_kernel (timed with the T-factor kernel: the whole call)"},
+        "roofline": roof,
         "cpu_baseline": {"value": cpu_tf, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
                          "sample": f"{ncs} of {nev} columns"},
         "parity": {"max_abs_err_vs_oracle": err, "columns": len(cols)},
-        "gpu_launches": 2 * args.steps, "clocks": clocks.summary(),
+        "gpu_launches": (2 if args.variant == "fp64" else 6) * args.steps, "clocks": clocks.summary(),
+        "variant": args.variant,
     }
     print(json.dumps(line), flush=True)
 

@@ -352,6 +352,29 @@ tbbt_status tbbt_trans_ev_band_to_full_z(const void *a, int64_t lda, const void 
                                          int64_t nev, void *q, int64_t ldq, void *stream);
 
 /* -------------------------------------------------------------------------
+ * Band -> full back-transformation, split-precision form on the tensor cores
+ * (Eq. 6e, real data): the same result as tbbt_trans_ev_band_to_full_d, with
+ * the 32-reflector WY blocks I - V T V^T applied as Y <- Y - U (V^T Y),
+ * U = V T, by exact products of 8-bit digit slices on BF16 tensor cores
+ * (tcgen05): Y in 64-bit fixed point per column (exponent from the column's
+ * norm), V and U in 6 digits scaled per block and per row, W = V^T Y summed
+ * in 64-bit integers across 96-row batches and across the CTAs that share a
+ * 128-column strip. Error: a few units of 2^-48 of a column's norm per
+ * block, in practice ~1e-14 absolute on unit-norm columns.
+ *
+ * Arguments, layouts, ownership and the reflector store as for
+ * tbbt_trans_ev_band_to_full_d. Needs a GPU of compute capability 10.x
+ * (TBBT_ENOTSUP otherwise) and a cooperative launch of one CTA per SM.
+ * Allocates stream-ordered workspace of about 24 * n^2 / 2 bytes of digit
+ * slices plus 8 * n * nev bytes for the fixed-point Y (13 GB + 2.6 GB at
+ * n = 32768, nev = 9830). A wait between CTAs that exceeds 20 s records
+ * TBBT_ETIMEOUT (tbbt_stream_check reports it).
+ * Errors: as tbbt_trans_ev_band_to_full_d, plus TBBT_ENOTSUP.
+ * ------------------------------------------------------------------------- */
+tbbt_status tbbt_trans_ev_band_to_full_split_d(const double *a, int64_t lda, const double *tau, int64_t n,
+                                               int64_t nbw, int64_t nev, double *q, int64_t ldq, void *stream);
+
+/* -------------------------------------------------------------------------
  * FP64 rate probe (a measurement aid; the paper has no counterpart). The
  * FP64 back-transformation is bound by the FP64 pipe, so its roofline
  * denominator is that pipe's rate, measured on the device in use:

@@ -96,7 +96,8 @@ def load():
             f = getattr(L, name)
             f.restype = c_int
             f.argtypes = [p, i64, i64, i64, p, p, p, p, p]
-        for name in ("tbbt_trans_ev_band_to_full_d", "tbbt_trans_ev_band_to_full_z"):
+        for name in ("tbbt_trans_ev_band_to_full_d", "tbbt_trans_ev_band_to_full_z",
+                     "tbbt_trans_ev_band_to_full_split_d"):
             f = getattr(L, name)
             f.restype = c_int
             f.argtypes = [p, i64, p, i64, i64, i64, p, i64, p]

@@ -212,13 +212,17 @@ def tridiag_eig(d, e, nev: int, complex_out: bool = False, x=None, stream=None):
     return w, x
 
 
-def trans_ev_band_to_full(a, tau, n: int, nbw: int, nev: int, q, stream=None):
+def trans_ev_band_to_full(a, tau, n: int, nbw: int, nev: int, q, stream=None, variant: int = 0):
     """Eq. 6e on device tensors: q[:n, :nev] <- H_0 ... H_{n-nbw-1} q[:n, :nev]
     with the full -> band reflectors held LAPACK-style below the band of
     ``a`` (n x n, column-major; reflector c has v[0] = 1 at row c+nbw and
     v[1:] in a[c+nbw+1:, c]) and ``tau`` (n-nbw entries). float64 or
-    complex128 CUDA tensors; q column-major."""
+    complex128 CUDA tensors; q column-major. ``variant``: VARIANT_FP64 (0)
+    or, for float64 data, VARIANT_SPLIT_BF16_TC (2), the digit-slice form on
+    the tensor cores."""
     cplx = _is_complex_dtype(q)
+    if variant not in (VARIANT_FP64, VARIANT_SPLIT_BF16_TC) or (cplx and variant != VARIANT_FP64):
+        raise ValueError("variant must be VARIANT_FP64, or VARIANT_SPLIT_BF16_TC for float64 data")
     K1 = max(n - nbw, 0) if nbw >= 1 else 0
     if K1 > 0 and nev > 0:
         if a.dim() != 2 or a.shape[0] < n or a.shape[1] < K1 or (a.shape[1] > 1 and a.stride(0) != 1):
@@ -231,7 +235,12 @@ def trans_ev_band_to_full(a, tau, n: int, nbw: int, nev: int, q, stream=None):
     lda = a.stride(1) if a.shape[1] > 1 else max(a.shape[0], 1)
     ldq, _ = _q_layout(q, n)
     L = _native.load()
-    f = L.tbbt_trans_ev_band_to_full_z if cplx else L.tbbt_trans_ev_band_to_full_d
+    if cplx:
+        f = L.tbbt_trans_ev_band_to_full_z
+    elif variant == VARIANT_SPLIT_BF16_TC:
+        f = L.tbbt_trans_ev_band_to_full_split_d
+    else:
+        f = L.tbbt_trans_ev_band_to_full_d
 
     def ptr(t):
         return ctypes.c_void_p(t.data_ptr() if t.numel() else 0)

@@ -20,6 +20,7 @@
 #include "tc_split.cuh"
 #include "bulge.cuh"
 #include "b2f.cuh"
+#include "b2f_split.cuh"
 #include "probe.cuh"
 #include "tridiag.cuh"
 
@@ -1296,4 +1297,159 @@ tbbt_status tridiag_eig_impl(const double *d, const double *e, int64_t n, int64_
 extern "C" tbbt_status tbbt_tridiag_eig(const double *d, const double *e, int64_t n, int64_t nev, double *w,
                                         void *x, int64_t ldx, tbbt_dtype xtype, void *stream) {
   return tridiag_eig_impl(d, e, n, nev, w, x, ldx, xtype, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// Band -> full back-transformation (Eq. 6e), split-precision form on tcgen05
+// ---------------------------------------------------------------------------
+namespace {
+tbbt_status band_to_full_split_impl(const double *a, int64_t lda, const double *tau, int64_t n, int64_t nbw,
+                                    int64_t nev, double *q, int64_t ldq, cudaStream_t s) {
+  namespace bfs = tbbt::bfs;
+  namespace bf = tbbt::bf;
+  namespace tcs = tbbt::tcs;
+  using D = bfs::D;
+  if (n < 0 || n > (int64_t)1 << 30 || nbw < 1 || nev < 0 || nev > n) return TBBT_EINVAL;
+  if (lda < std::max<int64_t>(1, n) || ldq < std::max<int64_t>(1, n)) return TBBT_EINVAL;
+  const int64_t K1 = n > nbw ? n - nbw : 0;
+  if (K1 == 0 || nev == 0) return TBBT_OK;
+  if (!a || !tau || !q) return TBBT_EINVAL;
+  if (((uintptr_t)q | (uintptr_t)a | (uintptr_t)tau) % alignof(double) != 0) return TBBT_EINVAL;
+  int dev = 0, major = 0, sms = 0;
+  TBBT_CUDA_TRY(cudaGetDevice(&dev));
+  TBBT_CUDA_TRY(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
+  if (major != 10) return TBBT_ENOTSUP;
+  TBBT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  // layout: 32-reflector blocks, 32-row tiles dealt to S_K slots per 128-column strip
+  bfs::Layout L;
+  L.n = (int32_t)n;
+  L.b = (int32_t)std::min<int64_t>(nbw, n);
+  L.K1 = (int32_t)K1;
+  L.P = (int32_t)((K1 + bf::NB - 1) / bf::NB);
+  L.ntiles = (int32_t)((n + 31) / 32);
+  const int32_t strips = (int32_t)((nev + tcs::WS - 1) / tcs::WS);
+  // S_K CTAs per strip, one CTA per SM: the fewest rounds of strips per CTA
+  // group, each round taking about 1 / S_K of a strip's work (ties: fewer
+  // slots, less exchange)
+  {
+    double best = 0.0;
+    L.SK = 1;
+    for (int32_t sk = 1; sk <= 8 && sk <= sms; ++sk) {
+      const int32_t conc = std::max(sms / sk, 1);
+      const double t = (double)((strips + conc - 1) / conc) / sk;
+      if (sk == 1 || t < best * 0.999) {
+        best = t;
+        L.SK = sk;
+      }
+    }
+  }
+  std::vector<bfs::Item> items;
+  std::vector<int32_t> item_base((size_t)L.P * L.SK), need_cum((size_t)L.P);
+  for (int32_t p = 0; p < L.P; ++p)
+    for (int32_t k = 0; k < L.SK; ++k) {
+      item_base[(size_t)p * L.SK + k] = (int32_t)items.size();
+      const int32_t nb = bfs::slot_batches(L, p, k);
+      for (int32_t bt = 0; bt < nb; ++bt) items.push_back(bfs::Item{p, k, bt, 0});
+    }
+  {
+    int32_t acc = 0;
+    for (int32_t p = L.P - 1; p >= 0; --p) {
+      for (int32_t k = 0; k < L.SK; ++k) acc += bfs::slot_batches(L, p, k) > 0;
+      need_cum[(size_t)p] = acc;
+    }
+  }
+  const int64_t ldz = (n + 3) & ~(int64_t)1;
+  const int32_t grid = L.SK * std::min(strips, std::max(sms / L.SK, 1));  // <= sms
+  // workspace (stream-ordered)
+  const size_t b_T = round256(sizeof(double) * (size_t)L.P * bf::NB * bf::NB);
+  const size_t b_gv = round256(sizeof(int32_t) * (size_t)L.P);
+  const size_t b_items = round256(sizeof(bfs::Item) * items.size());
+  const size_t b_base = round256(sizeof(int32_t) * item_base.size());
+  const size_t b_need = round256(sizeof(int32_t) * need_cum.size());
+  const size_t b_sl = round256((size_t)D::BLOCK_BYTES * items.size());
+  const size_t b_z = round256(sizeof(int64_t) * (size_t)nev * (size_t)ldz);
+  const size_t b_ce = round256(sizeof(int32_t) * (size_t)nev);
+  const size_t b_wp = round256(sizeof(int64_t) * (size_t)strips * 2 * L.SK * bf::NB * tcs::WS);
+  const size_t b_wc = round256(sizeof(unsigned) * (size_t)strips);
+  const size_t total = b_T + b_gv + b_items + b_base + b_need + b_sl + b_z + b_ce + b_wp + b_wc;
+  unsigned char *ws = nullptr;
+  TBBT_CUDA_TRY(cudaMallocAsync((void **)&ws, total, s));
+  tbbt_status rs = TBBT_OK;
+  do {
+    unsigned char *p0 = ws;
+    double *Tws = (double *)p0; p0 += b_T;
+    int32_t *gv = (int32_t *)p0; p0 += b_gv;
+    bfs::Item *d_items = (bfs::Item *)p0; p0 += b_items;
+    int32_t *d_base = (int32_t *)p0; p0 += b_base;
+    int32_t *d_need = (int32_t *)p0; p0 += b_need;
+    unsigned char *slices = p0; p0 += b_sl;
+    int64_t *zfix = (int64_t *)p0; p0 += b_z;
+    int32_t *colexp = (int32_t *)p0; p0 += b_ce;
+    int64_t *wpart = (int64_t *)p0; p0 += b_wp;
+    unsigned *wcnt = (unsigned *)p0;
+    // the host vectors live until the end of this call: the copies below are
+    // ordered on s before any kernel that reads them, and are from pageable
+    // memory, which the runtime stages before returning
+    if (cudaMemcpyAsync(d_items, items.data(), sizeof(bfs::Item) * items.size(), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(d_base, item_base.data(), sizeof(int32_t) * item_base.size(), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(d_need, need_cum.data(), sizeof(int32_t) * need_cum.size(), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemsetAsync(wcnt, 0, sizeof(unsigned) * (size_t)strips, s) != cudaSuccess ||
+        cudaMemsetAsync(zfix, 0, sizeof(int64_t) * (size_t)nev * (size_t)ldz, s) != cudaSuccess) {
+      rs = TBBT_ECUDA;
+      break;
+    }
+    bf::Geo g;
+    g.a = a;
+    g.lda = lda;
+    g.tau = tau;
+    g.n = (int32_t)n;
+    g.b = L.b;
+    g.K1 = (int32_t)K1;
+    g.P = L.P;
+    bf::bf_tfactor_kernel<double><<<L.P, bf::THREADS, 0, s>>>(g, Tws);
+    bfs::bfs_colnorm_kernel<<<L.P, 256, 0, s>>>(g, gv);
+    bfs::bfs_prepare_kernel<<<(unsigned)items.size(), 128, 0, s>>>(g, L, d_items, Tws, gv, slices);
+    const unsigned cblocks = (unsigned)((nev + 7) / 8);
+    tcs::to_fixed_kernel<<<cblocks, 256, 0, s>>>(q, ldq, zfix, ldz, (int32_t)n, (int32_t)nev, colexp);
+    if (cudaGetLastError() != cudaSuccess) { rs = TBBT_ECUDA; break; }
+    if (allow_max_dynamic_smem(bfs::bfs_apply_kernel) != cudaSuccess) { rs = TBBT_ECUDA; break; }
+    bfs::BfsArgs A;
+    A.z = zfix;
+    A.ldz = ldz;
+    A.L = L;
+    A.nev = (int32_t)nev;
+    A.strips = strips;
+    A.slices = slices;
+    A.gv = gv;
+    A.item_base = d_base;
+    A.need_cum = d_need;
+    A.wpart = wpart;
+    A.wcnt = wcnt;
+    int *err = nullptr;
+    if (cudaGetSymbolAddress((void **)&err, g_tbbt_error) != cudaSuccess) { rs = TBBT_ECUDA; break; }
+    A.err = err;
+    A.timeout_ns = 20000000000LL;
+    // the slots of a strip wait for one another: a cooperative launch
+    // guarantees that all CTAs are resident at once (or fails)
+    void *kargs[] = {&A};
+    if (cudaLaunchCooperativeKernel((const void *)bfs::bfs_apply_kernel, dim3((unsigned)grid), dim3(D::NTHREADS),
+                                    kargs, (size_t)D::SMEM, s) != cudaSuccess) {
+      rs = TBBT_ECUDA;
+      break;
+    }
+    tcs::from_fixed_kernel<<<cblocks, 256, 0, s>>>(q, ldq, zfix, ldz, (int32_t)n, (int32_t)nev, colexp);
+    if (cudaGetLastError() != cudaSuccess) rs = TBBT_ECUDA;
+  } while (0);
+  cudaFreeAsync(ws, s);
+  return rs;
+}
+}  // namespace
+
+extern "C" tbbt_status tbbt_trans_ev_band_to_full_split_d(const double *a, int64_t lda, const double *tau, int64_t n,
+                                                          int64_t nbw, int64_t nev, double *q, int64_t ldq,
+                                                          void *stream) {
+  return band_to_full_split_impl(a, lda, tau, n, nbw, nev, q, ldq, (cudaStream_t)stream);
 }

@@ -598,7 +598,6 @@ template <int B>
 __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a, const __grid_constant__ CUtensorMap zmap) {
   using D = Geo<B>;
   constexpr int P = D::P;
-  constexpr int RP = D::RP;
   extern __shared__ __align__(1024) unsigned char smem_dyn[];
   // the swizzled staging boxes need a 1024-byte aligned base
   unsigned char *const smem = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);

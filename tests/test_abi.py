@@ -131,7 +131,7 @@ def test_band_to_full_argument_checks(L):
     buf = (ctypes.c_double * 4)()
     p = ctypes.cast(buf, ctypes.c_void_p)
     EINVAL = 1
-    for f in (L.tbbt_trans_ev_band_to_full_d, L.tbbt_trans_ev_band_to_full_z):
+    for f in (L.tbbt_trans_ev_band_to_full_d, L.tbbt_trans_ev_band_to_full_z, L.tbbt_trans_ev_band_to_full_split_d):
         assert f(p, 10, p, 10, 0, 5, p, 10, None) == EINVAL  # nbw < 1
         assert f(p, 10, p, 10, 4, 11, p, 10, None) == EINVAL  # nev > n
         assert f(p, 10, p, 10, 4, -1, p, 10, None) == EINVAL  # nev < 0
@@ -146,6 +146,7 @@ def test_band_to_full_argument_checks(L):
         assert f(None, 1, None, 0, 4, 0, None, 1, None) == 0  # n = 0
     odd = ctypes.c_void_p(ctypes.addressof(buf) + 4)
     assert L.tbbt_trans_ev_band_to_full_d(p, 10, p, 10, 4, 5, odd, 10, None) == EINVAL  # misaligned q
+    assert L.tbbt_trans_ev_band_to_full_split_d(p, 10, p, 10, 4, 5, odd, 10, None) == EINVAL
 
 
 def test_bulge_chase_shape_limits_on_the_host(L):

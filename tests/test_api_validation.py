@@ -45,6 +45,13 @@ def test_band_to_full_rejects_bad_arguments():
         P.trans_ev_band_to_full(f64(n, n - 1).t(), f64(n - b), n, b, nev, q)  # 9 rows
     with pytest.raises(ValueError, match="2-D"):
         P.trans_ev_band_to_full(f64(n * n), f64(n - b), n, b, nev, q)
+    # the split-precision form takes real data only; variant 1 has no band -> full form
+    with pytest.raises(ValueError, match="variant"):
+        P.trans_ev_band_to_full(c128(n, n).t(), c128(n - b), n, b, nev, c128(nev, n).t(), variant=2)
+    with pytest.raises(ValueError, match="variant"):
+        P.trans_ev_band_to_full(a, f64(n - b), n, b, nev, q, variant=1)
+    with pytest.raises(ValueError, match="CUDA"):
+        P.trans_ev_band_to_full(a, f64(n - b), n, b, nev, q, variant=2)
 
 
 def test_bulge_chase_rejects_host_and_short_bands():
