@@ -16,10 +16,12 @@
 // (tile t belongs to slot t mod S_K), so that every CTA reads and updates
 // only its own tiles of Y, block after block: no exchange of Y between CTAs.
 // Per block the slots publish their partial W in global memory (one buffer
-// per slot and block parity), count themselves in on a per-strip counter,
+// per slot and block parity), count themselves in on the block's counter,
 // and every slot sums all partials once the counter says they are there
 // (bounded wait); then each slot normalises W, splits it into digits and
-// applies the update to its tiles.
+// applies the update to its tiles. The counters are per block: a slot with
+// no rows in block p skips it, so it may publish block p - 1 before block p
+// is complete, and a counter shared across blocks would count that too.
 //
 // Per batch a CTA (24 math warps: three 32-row parts x two 16-row halves x
 // 128 columns, one producer warp) runs, as the tcgen05 Eq. 6d kernel does
@@ -206,9 +208,9 @@ struct BfsArgs {
   const unsigned char *slices;   // items x BLOCK_BYTES
   const int32_t *gv;             // per WY block
   const int32_t *item_base;      // per (p, k): index of its first item
-  const int32_t *need_cum;       // per p: publications of blocks P-1 .. p (slots with rows, summed)
+  const int32_t *need;           // per p: slots with rows in block p
   int64_t *wpart;                // [strips][2][SK][NB][WS]: partial W per block parity and slot
-  unsigned *wcnt;                // per strip: partial W published so far
+  unsigned *wcnt;                // [strips][P]: partial W of the block published so far
   int *err;
   long long timeout_ns;
 };
@@ -463,8 +465,11 @@ __global__ void __launch_bounds__(D::NTHREADS, 1) bfs_apply_kernel(BfsArgs a) {
           ++n_batch;
         }
         if (nbat > 0) {
-          // ---- this slot's partial W -> global memory; count it in; wait
-          // (bounded) until every slot with rows in blocks P-1 .. p has
+          // ---- this slot's partial W -> global memory; count it in on the
+          // block's counter; wait (bounded) until every slot with rows in the
+          // block has. Buffer parity: a slot writes block p - 2's partial only
+          // after every slot with rows in p - 1 (a superset of those in p)
+          // published p - 1, which each did after reading block p's.
           int64_t *wp = a.wpart + ((((int64_t)strip * 2 + (p & 1)) * SK) * NB) * WS;
           if (ok) {
 #pragma unroll
@@ -476,13 +481,14 @@ __global__ void __launch_bounds__(D::NTHREADS, 1) bfs_apply_kernel(BfsArgs a) {
             if (s_abort) {
               atomicCAS(a.err, 0, 4 /* TBBT_ETIMEOUT */);  // the other slots stop waiting for this one
             } else {
+              unsigned *cnt_p = a.wcnt + (int64_t)strip * L.P + p;
               __threadfence();
-              atomicAdd(a.wcnt + strip, 1u);
-              const unsigned need = (unsigned)a.need_cum[p];
+              atomicAdd(cnt_p, 1u);
+              const unsigned need = (unsigned)a.need[p];
               const long long t0 = globaltimer_ns();
               for (unsigned itr = 0;; ++itr) {
                 unsigned v;
-                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(a.wcnt + strip) : "memory");
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(cnt_p) : "memory");
                 if (v >= need) break;
                 if (*(volatile int *)a.err != 0) { s_abort = 1; break; }
                 if (globaltimer_ns() - t0 > a.timeout_ns) {

@@ -1344,20 +1344,14 @@ tbbt_status band_to_full_split_impl(const double *a, int64_t lda, const double *
     }
   }
   std::vector<bfs::Item> items;
-  std::vector<int32_t> item_base((size_t)L.P * L.SK), need_cum((size_t)L.P);
+  std::vector<int32_t> item_base((size_t)L.P * L.SK), need((size_t)L.P, 0);
   for (int32_t p = 0; p < L.P; ++p)
     for (int32_t k = 0; k < L.SK; ++k) {
       item_base[(size_t)p * L.SK + k] = (int32_t)items.size();
       const int32_t nb = bfs::slot_batches(L, p, k);
       for (int32_t bt = 0; bt < nb; ++bt) items.push_back(bfs::Item{p, k, bt, 0});
+      need[(size_t)p] += nb > 0;
     }
-  {
-    int32_t acc = 0;
-    for (int32_t p = L.P - 1; p >= 0; --p) {
-      for (int32_t k = 0; k < L.SK; ++k) acc += bfs::slot_batches(L, p, k) > 0;
-      need_cum[(size_t)p] = acc;
-    }
-  }
   const int64_t ldz = (n + 3) & ~(int64_t)1;
   const int32_t grid = L.SK * std::min(strips, std::max(sms / L.SK, 1));  // <= sms
   // workspace (stream-ordered)
@@ -1365,12 +1359,12 @@ tbbt_status band_to_full_split_impl(const double *a, int64_t lda, const double *
   const size_t b_gv = round256(sizeof(int32_t) * (size_t)L.P);
   const size_t b_items = round256(sizeof(bfs::Item) * items.size());
   const size_t b_base = round256(sizeof(int32_t) * item_base.size());
-  const size_t b_need = round256(sizeof(int32_t) * need_cum.size());
+  const size_t b_need = round256(sizeof(int32_t) * need.size());
   const size_t b_sl = round256((size_t)D::BLOCK_BYTES * items.size());
   const size_t b_z = round256(sizeof(int64_t) * (size_t)nev * (size_t)ldz);
   const size_t b_ce = round256(sizeof(int32_t) * (size_t)nev);
   const size_t b_wp = round256(sizeof(int64_t) * (size_t)strips * 2 * L.SK * bf::NB * tcs::WS);
-  const size_t b_wc = round256(sizeof(unsigned) * (size_t)strips);
+  const size_t b_wc = round256(sizeof(unsigned) * (size_t)strips * L.P);
   const size_t total = b_T + b_gv + b_items + b_base + b_need + b_sl + b_z + b_ce + b_wp + b_wc;
   unsigned char *ws = nullptr;
   TBBT_CUDA_TRY(cudaMallocAsync((void **)&ws, total, s));
@@ -1394,9 +1388,9 @@ tbbt_status band_to_full_split_impl(const double *a, int64_t lda, const double *
             cudaSuccess ||
         cudaMemcpyAsync(d_base, item_base.data(), sizeof(int32_t) * item_base.size(), cudaMemcpyHostToDevice, s) !=
             cudaSuccess ||
-        cudaMemcpyAsync(d_need, need_cum.data(), sizeof(int32_t) * need_cum.size(), cudaMemcpyHostToDevice, s) !=
+        cudaMemcpyAsync(d_need, need.data(), sizeof(int32_t) * need.size(), cudaMemcpyHostToDevice, s) !=
             cudaSuccess ||
-        cudaMemsetAsync(wcnt, 0, sizeof(unsigned) * (size_t)strips, s) != cudaSuccess ||
+        cudaMemsetAsync(wcnt, 0, sizeof(unsigned) * (size_t)strips * L.P, s) != cudaSuccess ||
         cudaMemsetAsync(zfix, 0, sizeof(int64_t) * (size_t)nev * (size_t)ldz, s) != cudaSuccess) {
       rs = TBBT_ECUDA;
       break;
@@ -1425,7 +1419,7 @@ tbbt_status band_to_full_split_impl(const double *a, int64_t lda, const double *
     A.slices = slices;
     A.gv = gv;
     A.item_base = d_base;
-    A.need_cum = d_need;
+    A.need = d_need;
     A.wpart = wpart;
     A.wcnt = wcnt;
     int *err = nullptr;
