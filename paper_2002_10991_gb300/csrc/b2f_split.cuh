@@ -200,8 +200,47 @@ __global__ void __launch_bounds__(128) bfs_prepare_kernel(bf::Geo g, Layout L, c
   }
 }
 
+// Shared memory of the apply kernel: W's digits (GEMM2's A operand), two
+// buffers each of V' and U' (the next batch's operands load during the
+// current batch's products), the partial maxima of the column exchanges.
+constexpr int SM_W = 0;
+constexpr int SM_V = SM_W + S * D::WDIG;
+constexpr int SM_U = SM_V + 2 * D::VBYTES;
+constexpr int SM_KMX = SM_U + 2 * D::UBYTES;
+constexpr int SM_BYTES = SM_KMX + 2 * D::NSUB * WS * 8 + 1024;  // + room to align the base to 1024 bytes
+static_assert(SM_BYTES <= 227 * 1024, "shared memory of the split band -> full kernel");
+
+// 16 rows of one column from the fixed-point Y (16-byte pairs; rows >= n and
+// invalid tiles read as zero), plus `add`
+__device__ __forceinline__ void load_rows16(const int64_t *zc, int32_t rb, int32_t n, bool valid, int64_t add,
+                                            int64_t (&z)[16]) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int32_t r = rb + 2 * i;
+    if (valid && r + 1 < n) {
+      const longlong2 v = __ldcg(reinterpret_cast<const longlong2 *>(zc + r));
+      z[2 * i] = v.x + add;
+      z[2 * i + 1] = v.y + add;
+    } else if (valid && r < n) {
+      z[2 * i] = (int64_t)__ldcg((const long long *)(zc + r)) + add;
+      z[2 * i + 1] = add;
+    } else {
+      z[2 * i] = add;
+      z[2 * i + 1] = add;
+    }
+  }
+}
+__device__ __forceinline__ void store_rows16(int64_t *zc, int32_t rb, int32_t n, const int64_t (&z)[16]) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int32_t r = rb + 2 * i;
+    if (r + 1 < n) __stcg(reinterpret_cast<longlong2 *>(zc + r), make_longlong2(z[2 * i], z[2 * i + 1]));
+    else if (r < n) __stcg((long long *)(zc + r), (long long)z[2 * i]);
+  }
+}
+
 struct BfsArgs {
-  int64_t *z;  // fixed-point Y: column c, row r at c * ldz + r + 1 (tcs::to_fixed_kernel)
+  int64_t *z;  // fixed-point Y: column c, row r at c * ldz + r (16-byte aligned for even r; ldz even)
   int64_t ldz;
   Layout L;
   int32_t nev, strips;
@@ -216,12 +255,32 @@ struct BfsArgs {
 };
 
 struct BfsBarriers {
-  uint64_t zfull[S], blk, g1, wfull, c[3], cfree, v, u, drain;
+  uint64_t zfull[S], blk, g1, wfull, c[3], cfree, v[2], u[2], drain;
 };
 
-// x 2^-s rounded to the nearest integer (ties up), s >= 0.
-__device__ __forceinline__ int64_t rshift_round(int64_t x, int s) {
-  return s > 0 ? ((x + ((int64_t)1 << (s - 1))) >> s) : x;
+// Levels of W = V'^T Z for C consecutive reflectors of this thread's column
+// (as tc_split.cuh's w_levels, one level at a time: fewer live registers),
+// at the batch's shift zsh, rounded back to the unshifted scale and added to
+// acc[0], acc[WS], ... (the block's sums in shared memory).
+template <int C>
+__device__ __forceinline__ void w_levels_acc(uint32_t taddr, int zsh, int64_t *acc) {
+  int64_t w[C];
+#pragma unroll
+  for (int l = 0; l < LV; ++l) {
+    uint32_t r[C];
+    if constexpr (C == 8) tmem_ld8(taddr + 32 * l, r);
+    else tmem_ld4(taddr + 32 * l, r);
+    tc_wait_ld();
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+      const int32_t v = __float2int_rn(__uint_as_float(r[i]));  // |v| < 2^24: exact
+      if (l == 0) w[i] = v;
+      else if (l < LV - 1) w[i] = shl8_add(w[i], v);
+      else w[i] = (int64_t)((uint64_t)w[i] << 2) + (v >> 6);  // 4 h + floor(a_6 / 64)
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < C; ++i) acc[i * WS] += zsh > 0 ? ((w[i] + ((int64_t)1 << (zsh - 1))) >> zsh) : w[i];
 }
 
 __global__ void __launch_bounds__(D::NTHREADS, 1) bfs_apply_kernel(BfsArgs a) {
@@ -256,8 +315,10 @@ __global__ void __launch_bounds__(D::NTHREADS, 1) bfs_apply_kernel(BfsArgs a) {
     mbar_init(&bars.wfull, D::NMATH);
     for (int p = 0; p < 3; ++p) mbar_init(&bars.c[p], 1);
     mbar_init(&bars.cfree, 128 * D::H);
-    mbar_init(&bars.v, 1);
-    mbar_init(&bars.u, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&bars.v[b], 1);
+      mbar_init(&bars.u[b], 1);
+    }
     mbar_init(&bars.drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     s_abort = 0;
@@ -273,7 +334,10 @@ __global__ void __launch_bounds__(D::NTHREADS, 1) bfs_apply_kernel(BfsArgs a) {
   uint32_t n_a = 0;      // pass-A batches: zfull, g1
   uint32_t n_c = 0;      // pass-C batches: c[*], cfree
   uint32_t n_w = 0;      // blocks: wfull
-  uint32_t n_v = 0, n_u = 0, iss_v = 0, iss_u = 0;
+  // operand loads: batch i of a pass (counted over the whole launch) uses
+  // buffer i & 1 and is the (i >> 1)-th load into it
+  uint32_t iss_v[2] = {0, 0}, iss_u[2] = {0, 0};  // loads issued per buffer (for the drain)
+  bool pre_v = false;  // V' of the block's first batch is already on its way
   const int slot = blockIdx.x % SK;
   const int rounds_stride = gridDim.x / SK;
 
@@ -288,17 +352,32 @@ __global__ void __launch_bounds__(D::NTHREADS, 1) bfs_apply_kernel(BfsArgs a) {
       if (producer) {
         if (lane == 0) {
           // ----------------------------------------------------------- producer
-          const uint32_t vbase = smem_u32(smem + D::OFF_V);
-          const uint32_t ubase = smem_u32(smem + D::OFF_U);
-          const uint32_t wbase = smem_u32(smem + D::OFF_W);
+          const uint32_t wbase = smem_u32(smem + SM_W);
+          auto load_v = [&](uint32_t i, int32_t bt, const unsigned char *it0) {
+            const int bf = i & 1;
+            mbar_expect_tx(&bars.v[bf], D::VBYTES);
+            bulk_load(smem + SM_V + bf * D::VBYTES, it0 + (int64_t)bt * D::BLOCK_BYTES, D::VBYTES, &bars.v[bf]);
+            ++iss_v[bf];
+          };
+          auto load_u = [&](uint32_t i, int32_t bt, const unsigned char *it0) {
+            const int bf = i & 1;
+            mbar_expect_tx(&bars.u[bf], D::UBYTES);
+            bulk_load(smem + SM_U + bf * D::UBYTES, it0 + (int64_t)bt * D::BLOCK_BYTES + D::VBYTES, D::UBYTES,
+                      &bars.u[bf]);
+            ++iss_u[bf];
+          };
           bool ok = true;
+          // U' of this block's first pass-C batch: its buffer is free (every
+          // earlier GEMM2 is complete)
+          if (nbat > 0) load_u(n_c, 0, items0);
           // pass A: GEMM1 per batch
           for (int32_t bt = 0; bt < nbat && ok; ++bt) {
-            mbar_expect_tx(&bars.v, D::VBYTES);
-            bulk_load(smem + D::OFF_V, items0 + (int64_t)bt * D::BLOCK_BYTES, D::VBYTES, &bars.v);
-            ++iss_v;
-            if (!mbar_wait(&bars.v, n_v & 1, &s_abort, a.err, a.timeout_ns)) { ok = false; break; }
-            ++n_v;
+            if (bt == 0 && !pre_v) load_v(n_a, 0, items0);
+            pre_v = false;
+            // the other buffer's GEMM1 (batch n_a - 1) is complete
+            if (bt + 1 < nbat) load_v(n_a + 1, bt + 1, items0);
+            if (!mbar_wait(&bars.v[n_a & 1], (n_a >> 1) & 1, &s_abort, a.err, a.timeout_ns)) { ok = false; break; }
+            const uint32_t vbase = smem_u32(smem + SM_V + (n_a & 1) * D::VBYTES);
             for (int k = 0; k < S; ++k) {
               if (!mbar_wait(&bars.zfull[k], n_a & 1, &s_abort, a.err, a.timeout_ns)) { ok = false; break; }
               tc_fence_after();
@@ -321,14 +400,17 @@ __global__ void __launch_bounds__(D::NTHREADS, 1) bfs_apply_kernel(BfsArgs a) {
             ++n_a;
             ++n_batch;
           }
+          // V' of the next block's first batch: both buffers are free now
+          if (ok && p > 0 && slot_batches(L, p - 1, slot) > 0) {
+            load_v(n_a, 0, a.slices + (int64_t)a.item_base[(p - 1) * SK + slot] * D::BLOCK_BYTES);
+            pre_v = true;
+          }
           // pass C: GEMM2 per batch and part (part 0 -> region A, 1 -> region B,
           // 2 -> region A once part 0 is read)
           for (int32_t bt = 0; bt < nbat && ok; ++bt) {
-            mbar_expect_tx(&bars.u, D::UBYTES);
-            bulk_load(smem + D::OFF_U, items0 + (int64_t)bt * D::BLOCK_BYTES + D::VBYTES, D::UBYTES, &bars.u);
-            ++iss_u;
-            if (!mbar_wait(&bars.u, n_u & 1, &s_abort, a.err, a.timeout_ns)) { ok = false; break; }
-            ++n_u;
+            // the other buffer's GEMM2 (batch n_c - 1) is complete
+            if (bt + 1 < nbat) load_u(n_c + 1, bt + 1, items0);
+            if (!mbar_wait(&bars.u[n_c & 1], (n_c >> 1) & 1, &s_abort, a.err, a.timeout_ns)) { ok = false; break; }
             if (bt == 0 && !mbar_wait(&bars.wfull, n_w & 1, &s_abort, a.err, a.timeout_ns)) { ok = false; break; }
             // every thread read the previous batch's accumulators
             if (n_batch > 0 && !mbar_wait(&bars.blk, (n_batch - 1) & 1, &s_abort, a.err, a.timeout_ns)) {
@@ -336,6 +418,7 @@ __global__ void __launch_bounds__(D::NTHREADS, 1) bfs_apply_kernel(BfsArgs a) {
               break;
             }
             tc_fence_after();
+            const uint32_t ubase = smem_u32(smem + SM_U + (n_c & 1) * D::UBYTES);
             for (int part = 0; part < P && ok; ++part) {
               if (part == 2) {
                 if (!mbar_wait(&bars.cfree, n_c & 1, &s_abort, a.err, a.timeout_ns)) { ok = false; break; }
@@ -372,8 +455,7 @@ __global__ void __launch_bounds__(D::NTHREADS, 1) bfs_apply_kernel(BfsArgs a) {
         // --------------------------------------------------------------- math
         const int64_t C = kDigitOffset;
         const bool colok = c0 + col < a.nev;
-        const int64_t *zcol = a.z + (int64_t)(c0 + col) * a.ldz + 1;
-        int64_t *zcolw = a.z + (int64_t)(c0 + col) * a.ldz + 1;
+        int64_t *const zcol = a.z + (int64_t)(c0 + col) * a.ldz;
         const int sub = D::H * grp + hf;
         // reflector range of this thread set in the W readout (8 / 4 / 4 / 4 / 4 / 8)
         const int ca0 = sub == 0 ? 0 : (sub == 5 ? 24 : 4 + 4 * sub);
@@ -383,25 +465,29 @@ __global__ void __launch_bounds__(D::NTHREADS, 1) bfs_apply_kernel(BfsArgs a) {
           const int32_t j = 3 * bt + grp;
           return j < cnt ? 32 * (f + j * SK) + RT * hf : -1;
         };
-        int64_t wacc[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) wacc[i] = 0;
+        // the block's W sums of my column and reflectors, in the W-digit
+        // buffer (free during pass A: the previous block's GEMM2 is complete
+        // once the first blk wait below returns); entry (m, col) at m WS + col
+        int64_t *const wacc = reinterpret_cast<int64_t *>(smem + SM_W) + ca0 * WS + col;
         // Every math thread runs the same sequence of named barriers whatever
         // happens: after an abort (ok false) the work is skipped, not the
         // barriers, so no warp is left waiting at one.
         bool ok = !s_abort;
-        // ---- pass A
+        // ---- pass A (the next batch's rows load while this batch's GEMM1 runs)
+        int64_t z[RT];
+        if (nbat > 0) {
+          const int32_t rb = my_row0(0);
+          load_rows16(zcol, rb, L.n, ok && rb >= 0 && colok, C, z);
+        }
         for (int32_t bt = 0; bt < nbat; ++bt) {
-          const int32_t rb = my_row0(bt);
-          int64_t z[RT];
-#pragma unroll
-          for (int i = 0; i < RT; ++i) {
-            const int32_t r = rb + i;
-            z[i] = (ok && rb >= 0 && colok && r < L.n) ? (int64_t)__ldcg((const long long *)(zcol + r)) + C : C;
-          }
           if (ok && n_batch > 0) {
             ok = mbar_wait(&bars.blk, (n_batch - 1) & 1, &s_abort, a.err, a.timeout_ns);
             tc_fence_after();
+          }
+          if (bt == 0) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+              if (i < cw0) wacc[i * WS] = 0;
           }
           // per-column shift of this batch (as the Eq. 6d kernel's per window):
           // every entry below 2^61 and the batch's 1-norm within 2^66
@@ -416,7 +502,7 @@ __global__ void __launch_bounds__(D::NTHREADS, 1) bfs_apply_kernel(BfsArgs a) {
               mz = m > mz ? m : mz;
               sz += (m + 31u) >> 5;
             }
-            uint32_t *kz = reinterpret_cast<uint32_t *>(smem + D::OFF_KMX);
+            uint32_t *kz = reinterpret_cast<uint32_t *>(smem + SM_KMX);
             kz[sub * WS + col] = mz;
             kz[(D::NSUB + sub) * WS + col] = sz;
             named_sync(1, D::NMATH);
@@ -446,18 +532,18 @@ __global__ void __launch_bounds__(D::NTHREADS, 1) bfs_apply_kernel(BfsArgs a) {
               tc_fence_before();
               mbar_arrive(&bars.zfull[k - 1]);
             }
-            ok = mbar_wait(&bars.g1, n_a & 1, &s_abort, a.err, a.timeout_ns);
           }
+          if (bt + 1 < nbat) {
+            const int32_t rb = my_row0(bt + 1);
+            load_rows16(zcol, rb, L.n, ok && rb >= 0 && colok, C, z);
+          }
+          if (ok) ok = mbar_wait(&bars.g1, n_a & 1, &s_abort, a.err, a.timeout_ns);
           if (ok) {
             tc_fence_after();
             // this batch's W levels, back to the unshifted scale, into the block's sum
-            int64_t w[8];
             const uint32_t wt = tmem + lane_base;
-            if (cw0 == 8) w_levels<8>(wt + ca0, w);
-            else w_levels<4>(wt + ca0, w);
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-              if (i < cw0) wacc[i] += rshift_round(w[i], zsh);
+            if (cw0 == 8) w_levels_acc<8>(wt + ca0, zsh, wacc);
+            else w_levels_acc<4>(wt + ca0, zsh, wacc);
             tc_fence_before();
             mbar_arrive(&bars.blk);
           }
@@ -474,7 +560,7 @@ __global__ void __launch_bounds__(D::NTHREADS, 1) bfs_apply_kernel(BfsArgs a) {
           if (ok) {
 #pragma unroll
             for (int i = 0; i < 8; ++i)
-              if (i < cw0) __stcg((long long *)(wp + ((int64_t)slot * NB + ca0 + i) * WS + col), (long long)wacc[i]);
+              if (i < cw0) __stcg((long long *)(wp + ((int64_t)slot * NB + ca0 + i) * WS + col), (long long)wacc[i * WS]);
           }
           named_sync(1, D::NMATH);
           if (tid == 0) {
@@ -516,7 +602,7 @@ __global__ void __launch_bounds__(D::NTHREADS, 1) bfs_apply_kernel(BfsArgs a) {
             const uint64_t ax = (uint64_t)(w[i] < 0 ? -w[i] : w[i]);
             mx = ax > mx ? ax : mx;
           }
-          uint64_t *kmx = reinterpret_cast<uint64_t *>(smem + D::OFF_KMX);
+          uint64_t *kmx = reinterpret_cast<uint64_t *>(smem + SM_KMX);
           kmx[sub * WS + col] = mx;
           named_sync(1, D::NMATH);
 #pragma unroll
@@ -527,7 +613,7 @@ __global__ void __launch_bounds__(D::NTHREADS, 1) bfs_apply_kernel(BfsArgs a) {
           const int bits = mx ? 64 - __clzll((long long)mx) : 0;
           const int kcol = (bits > 0 && bits < FOP) ? FOP - bits : 0;
           if (ok) {
-            unsigned char *wb = smem + D::OFF_W;
+            unsigned char *wb = smem + SM_W;
 #pragma unroll
             for (int i = 0; i < 8; ++i) w[i] = (int64_t)((uint64_t)w[i] << kcol) + C;
             const int koff = kmaj(col, ca0, NB);
@@ -556,12 +642,7 @@ __global__ void __launch_bounds__(D::NTHREADS, 1) bfs_apply_kernel(BfsArgs a) {
           // ---- pass C: corr of my rows, Z -= sum_l B_l 2^(rs + gu[r] - 8 l)
           for (int32_t bt = 0; bt < nbat && ok; ++bt) {
             const int32_t rb = my_row0(bt);
-            int64_t z[RT];
-#pragma unroll
-            for (int i = 0; i < RT; ++i) {
-              const int32_t r = rb + i;
-              z[i] = (rb >= 0 && colok && r < L.n) ? (int64_t)__ldcg((const long long *)(zcol + r)) : 0;
-            }
+            load_rows16(zcol, rb, L.n, rb >= 0 && colok, 0, z);
             uint32_t gu4[RT / 4];
             {
               const uint4 *gsrc = reinterpret_cast<const uint4 *>(items0 + (int64_t)bt * D::BLOCK_BYTES + D::VBYTES +
@@ -623,11 +704,7 @@ __global__ void __launch_bounds__(D::NTHREADS, 1) bfs_apply_kernel(BfsArgs a) {
             tc_fence_before();
             if (grp == 0) mbar_arrive(&bars.cfree);  // region A is free for part 2
             mbar_arrive(&bars.blk);
-            if (rb >= 0 && colok) {
-#pragma unroll
-              for (int i = 0; i < RT; ++i)
-                if (rb + i < L.n) __stcg((long long *)(zcolw + rb + i), (long long)z[i]);
-            }
+            if (rb >= 0 && colok) store_rows16(zcol, rb, L.n, z);
             ++n_c;
             ++n_batch;
           }
@@ -652,8 +729,10 @@ __global__ void __launch_bounds__(D::NTHREADS, 1) bfs_apply_kernel(BfsArgs a) {
     volatile int never = 0;
     const long long lim = 2000000000LL;
     mbar_wait(&bars.drain, 0, &never, a.err, lim);
-    if (iss_v) mbar_wait(&bars.v, (iss_v - 1) & 1, &never, a.err, lim);
-    if (iss_u) mbar_wait(&bars.u, (iss_u - 1) & 1, &never, a.err, lim);
+    for (int b = 0; b < 2; ++b) {  // the last load issued into each buffer has landed
+      if (iss_v[b]) mbar_wait(&bars.v[b], (iss_v[b] - 1) & 1, &never, a.err, lim);
+      if (iss_u[b]) mbar_wait(&bars.u[b], (iss_u[b] - 1) & 1, &never, a.err, lim);
+    }
   }
   tc_fence_before();
   __syncthreads();

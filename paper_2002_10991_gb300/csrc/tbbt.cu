@@ -1361,7 +1361,7 @@ tbbt_status band_to_full_split_impl(const double *a, int64_t lda, const double *
   const size_t b_base = round256(sizeof(int32_t) * item_base.size());
   const size_t b_need = round256(sizeof(int32_t) * need.size());
   const size_t b_sl = round256((size_t)D::BLOCK_BYTES * items.size());
-  const size_t b_z = round256(sizeof(int64_t) * (size_t)nev * (size_t)ldz);
+  const size_t b_z = round256(sizeof(int64_t) * ((size_t)nev * (size_t)ldz + 2));
   const size_t b_ce = round256(sizeof(int32_t) * (size_t)nev);
   const size_t b_wp = round256(sizeof(int64_t) * (size_t)strips * 2 * L.SK * bf::NB * tcs::WS);
   const size_t b_wc = round256(sizeof(unsigned) * (size_t)strips * L.P);
@@ -1391,7 +1391,7 @@ tbbt_status band_to_full_split_impl(const double *a, int64_t lda, const double *
         cudaMemcpyAsync(d_need, need.data(), sizeof(int32_t) * need.size(), cudaMemcpyHostToDevice, s) !=
             cudaSuccess ||
         cudaMemsetAsync(wcnt, 0, sizeof(unsigned) * (size_t)strips * L.P, s) != cudaSuccess ||
-        cudaMemsetAsync(zfix, 0, sizeof(int64_t) * (size_t)nev * (size_t)ldz, s) != cudaSuccess) {
+        cudaMemsetAsync(zfix, 0, sizeof(int64_t) * ((size_t)nev * (size_t)ldz + 2), s) != cudaSuccess) {
       rs = TBBT_ECUDA;
       break;
     }
@@ -1407,11 +1407,13 @@ tbbt_status band_to_full_split_impl(const double *a, int64_t lda, const double *
     bfs::bfs_colnorm_kernel<<<L.P, 256, 0, s>>>(g, gv);
     bfs::bfs_prepare_kernel<<<(unsigned)items.size(), 128, 0, s>>>(g, L, d_items, Tws, gv, slices);
     const unsigned cblocks = (unsigned)((nev + 7) / 8);
-    tcs::to_fixed_kernel<<<cblocks, 256, 0, s>>>(q, ldq, zfix, ldz, (int32_t)n, (int32_t)nev, colexp);
+    // the conversions put row r of column c at zfix + 1 + c ldz + r + 1: even
+    // rows on 16-byte boundaries (ldz is even), as the apply kernel's pairs need
+    tcs::to_fixed_kernel<<<cblocks, 256, 0, s>>>(q, ldq, zfix + 1, ldz, (int32_t)n, (int32_t)nev, colexp);
     if (cudaGetLastError() != cudaSuccess) { rs = TBBT_ECUDA; break; }
     if (allow_max_dynamic_smem(bfs::bfs_apply_kernel) != cudaSuccess) { rs = TBBT_ECUDA; break; }
     bfs::BfsArgs A;
-    A.z = zfix;
+    A.z = zfix + 2;
     A.ldz = ldz;
     A.L = L;
     A.nev = (int32_t)nev;
@@ -1430,11 +1432,11 @@ tbbt_status band_to_full_split_impl(const double *a, int64_t lda, const double *
     // guarantees that all CTAs are resident at once (or fails)
     void *kargs[] = {&A};
     if (cudaLaunchCooperativeKernel((const void *)bfs::bfs_apply_kernel, dim3((unsigned)grid), dim3(D::NTHREADS),
-                                    kargs, (size_t)D::SMEM, s) != cudaSuccess) {
+                                    kargs, (size_t)bfs::SM_BYTES, s) != cudaSuccess) {
       rs = TBBT_ECUDA;
       break;
     }
-    tcs::from_fixed_kernel<<<cblocks, 256, 0, s>>>(q, ldq, zfix, ldz, (int32_t)n, (int32_t)nev, colexp);
+    tcs::from_fixed_kernel<<<cblocks, 256, 0, s>>>(q, ldq, zfix + 1, ldz, (int32_t)n, (int32_t)nev, colexp);
     if (cudaGetLastError() != cudaSuccess) rs = TBBT_ECUDA;
   } while (0);
   cudaFreeAsync(ws, s);
