@@ -373,6 +373,17 @@ tbbt_status tbbt_trans_ev_band_to_full_z(const void *a, int64_t lda, const void 
  * ------------------------------------------------------------------------- */
 tbbt_status tbbt_trans_ev_band_to_full_split_d(const double *a, int64_t lda, const double *tau, int64_t n,
                                                int64_t nbw, int64_t nev, double *q, int64_t ldq, void *stream);
+/* The same with options. wait_timeout_ms: limit of each wait between CTAs
+ * (0: 20000). debug_withhold_cta: test hook, -1 in normal use; otherwise the
+ * CTA (strip-major: strip * S_K + slot) whose W publications are not
+ * counted, so that the waits of its strip run out, TBBT_ETIMEOUT is recorded
+ * and every CTA drains and exits (failure detection without a GPU fault).
+ * Errors: as above, plus TBBT_EINVAL for wait_timeout_ms < 0 or
+ * debug_withhold_cta < -1. */
+tbbt_status tbbt_trans_ev_band_to_full_split_opts_d(const double *a, int64_t lda, const double *tau, int64_t n,
+                                                    int64_t nbw, int64_t nev, double *q, int64_t ldq,
+                                                    int32_t wait_timeout_ms, int32_t debug_withhold_cta,
+                                                    void *stream);
 
 /* -------------------------------------------------------------------------
  * FP64 rate probe (a measurement aid; the paper has no counterpart). The

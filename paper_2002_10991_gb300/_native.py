@@ -101,6 +101,8 @@ def load():
             f = getattr(L, name)
             f.restype = c_int
             f.argtypes = [p, i64, p, i64, i64, i64, p, i64, p]
+        L.tbbt_trans_ev_band_to_full_split_opts_d.restype = c_int
+        L.tbbt_trans_ev_band_to_full_split_opts_d.argtypes = [p, i64, p, i64, i64, i64, p, i64, i32, i32, p]
         L.tbbt_tridiag_eig.restype = c_int
         L.tbbt_tridiag_eig.argtypes = [p, p, i64, i64, p, p, i64, c_int, p]
         L.tbbt_fp64_probe.restype = c_int

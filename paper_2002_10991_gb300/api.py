@@ -212,14 +212,17 @@ def tridiag_eig(d, e, nev: int, complex_out: bool = False, x=None, stream=None):
     return w, x
 
 
-def trans_ev_band_to_full(a, tau, n: int, nbw: int, nev: int, q, stream=None, variant: int = 0):
+def trans_ev_band_to_full(a, tau, n: int, nbw: int, nev: int, q, stream=None, variant: int = 0,
+                          wait_timeout_ms: int = 0, debug_withhold_cta: int = -1):
     """Eq. 6e on device tensors: q[:n, :nev] <- H_0 ... H_{n-nbw-1} q[:n, :nev]
     with the full -> band reflectors held LAPACK-style below the band of
     ``a`` (n x n, column-major; reflector c has v[0] = 1 at row c+nbw and
     v[1:] in a[c+nbw+1:, c]) and ``tau`` (n-nbw entries). float64 or
     complex128 CUDA tensors; q column-major. ``variant``: VARIANT_FP64 (0)
     or, for float64 data, VARIANT_SPLIT_BF16_TC (2), the digit-slice form on
-    the tensor cores."""
+    the tensor cores; for that form ``wait_timeout_ms`` bounds the waits
+    between its CTAs (0: 20 s) and ``debug_withhold_cta`` (a test hook, -1 in
+    normal use) makes one CTA's W publications go uncounted."""
     cplx = _is_complex_dtype(q)
     if variant not in (VARIANT_FP64, VARIANT_SPLIT_BF16_TC) or (cplx and variant != VARIANT_FP64):
         raise ValueError("variant must be VARIANT_FP64, or VARIANT_SPLIT_BF16_TC for float64 data")
@@ -245,7 +248,11 @@ def trans_ev_band_to_full(a, tau, n: int, nbw: int, nev: int, q, stream=None, va
     def ptr(t):
         return ctypes.c_void_p(t.data_ptr() if t.numel() else 0)
 
-    st = f(ptr(a), lda, ptr(tau), n, nbw, nev, ptr(q), ldq, _stream_handle(stream))
+    if variant == VARIANT_SPLIT_BF16_TC:
+        st = L.tbbt_trans_ev_band_to_full_split_opts_d(ptr(a), lda, ptr(tau), n, nbw, nev, ptr(q), ldq,
+                                                       wait_timeout_ms, debug_withhold_cta, _stream_handle(stream))
+    else:
+        st = f(ptr(a), lda, ptr(tau), n, nbw, nev, ptr(q), ldq, _stream_handle(stream))
     _check(st, "tbbt_trans_ev_band_to_full")
     return q
 

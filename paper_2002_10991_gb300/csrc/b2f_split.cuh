@@ -69,31 +69,9 @@ __host__ __device__ inline int32_t slot_batches(const Layout &L, int32_t p, int3
   return (slot_count(L, p, k) + 2) / 3;
 }
 
-// gv[p]: |V| of block p scaled by 2^(60 - gv) has every column norm below
-// 2^60, so every entry stays in range and, by Cauchy-Schwarz, so does every
-// partial W. One block of 256 threads per WY block: eight threads per
-// reflector.
-__global__ void __launch_bounds__(256) bfs_colnorm_kernel(bf::Geo g, int32_t *__restrict__ gv) {
-  __shared__ double part[256];
-  const int p = blockIdx.x, tid = threadIdx.x;
-  const int m = tid / 8, sub = tid % 8;
-  double ss = 0.0;
-  const int32_t c = 32 * p + m;
-  if (c < g.K1)
-    for (int32_t r = c + g.b + sub; r < g.n; r += 8) {
-      const double v = bf::vget<double>(g, r, p, m);
-      ss = fma(v, v, ss);
-    }
-  part[tid] = ss;
-  __syncthreads();
-  if (tid < 32) {
-    double s = 0.0;
-    for (int i = 0; i < 8; ++i) s += part[tid * 8 + i];
-    double mx = sqrt(s);
-    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (tid == 0) gv[p] = exp_of_bits(abs_bits(mx));
-  }
-}
+// gv[p] (from bf_tfactor_kernel): every reflector of block p has norm below
+// 2^gv, so V' = V 2^(60 - gv) has every entry, and by Cauchy-Schwarz every
+// partial W, in range.
 
 // The digit slices of one (block, slot, batch): V' (96 rows x 32 reflectors,
 // K-major for GEMM1's B operand) and U' = (V T)' (three 32-row parts for
@@ -252,6 +230,7 @@ struct BfsArgs {
   unsigned *wcnt;                // [strips][P]: partial W of the block published so far
   int *err;
   long long timeout_ns;
+  int32_t withhold;  // test hook: CTA whose W publications are not counted (-1: none)
 };
 
 struct BfsBarriers {
@@ -569,7 +548,7 @@ __global__ void __launch_bounds__(D::NTHREADS, 1) bfs_apply_kernel(BfsArgs a) {
             } else {
               unsigned *cnt_p = a.wcnt + (int64_t)strip * L.P + p;
               __threadfence();
-              atomicAdd(cnt_p, 1u);
+              if ((int32_t)blockIdx.x != a.withhold) atomicAdd(cnt_p, 1u);
               const unsigned need = (unsigned)a.need[p];
               const long long t0 = globaltimer_ns();
               for (unsigned itr = 0;; ++itr) {

@@ -1304,13 +1304,15 @@ extern "C" tbbt_status tbbt_tridiag_eig(const double *d, const double *e, int64_
 // ---------------------------------------------------------------------------
 namespace {
 tbbt_status band_to_full_split_impl(const double *a, int64_t lda, const double *tau, int64_t n, int64_t nbw,
-                                    int64_t nev, double *q, int64_t ldq, cudaStream_t s) {
+                                    int64_t nev, double *q, int64_t ldq, int32_t wait_timeout_ms,
+                                    int32_t debug_withhold_cta, cudaStream_t s) {
   namespace bfs = tbbt::bfs;
   namespace bf = tbbt::bf;
   namespace tcs = tbbt::tcs;
   using D = bfs::D;
   if (n < 0 || n > (int64_t)1 << 30 || nbw < 1 || nev < 0 || nev > n) return TBBT_EINVAL;
   if (lda < std::max<int64_t>(1, n) || ldq < std::max<int64_t>(1, n)) return TBBT_EINVAL;
+  if (wait_timeout_ms < 0 || debug_withhold_cta < -1) return TBBT_EINVAL;
   const int64_t K1 = n > nbw ? n - nbw : 0;
   if (K1 == 0 || nev == 0) return TBBT_OK;
   if (!a || !tau || !q) return TBBT_EINVAL;
@@ -1403,8 +1405,7 @@ tbbt_status band_to_full_split_impl(const double *a, int64_t lda, const double *
     g.b = L.b;
     g.K1 = (int32_t)K1;
     g.P = L.P;
-    bf::bf_tfactor_kernel<double><<<L.P, bf::THREADS, 0, s>>>(g, Tws);
-    bfs::bfs_colnorm_kernel<<<L.P, 256, 0, s>>>(g, gv);
+    bf::bf_tfactor_kernel<double><<<L.P, bf::THREADS, 0, s>>>(g, Tws, gv);
     bfs::bfs_prepare_kernel<<<(unsigned)items.size(), 128, 0, s>>>(g, L, d_items, Tws, gv, slices);
     const unsigned cblocks = (unsigned)((nev + 7) / 8);
     // the conversions put row r of column c at zfix + 1 + c ldz + r + 1: even
@@ -1427,7 +1428,8 @@ tbbt_status band_to_full_split_impl(const double *a, int64_t lda, const double *
     int *err = nullptr;
     if (cudaGetSymbolAddress((void **)&err, g_tbbt_error) != cudaSuccess) { rs = TBBT_ECUDA; break; }
     A.err = err;
-    A.timeout_ns = 20000000000LL;
+    A.timeout_ns = (wait_timeout_ms > 0 ? (long long)wait_timeout_ms : 20000LL) * 1000000LL;
+    A.withhold = debug_withhold_cta;
     // the slots of a strip wait for one another: a cooperative launch
     // guarantees that all CTAs are resident at once (or fails)
     void *kargs[] = {&A};
@@ -1447,5 +1449,12 @@ tbbt_status band_to_full_split_impl(const double *a, int64_t lda, const double *
 extern "C" tbbt_status tbbt_trans_ev_band_to_full_split_d(const double *a, int64_t lda, const double *tau, int64_t n,
                                                           int64_t nbw, int64_t nev, double *q, int64_t ldq,
                                                           void *stream) {
-  return band_to_full_split_impl(a, lda, tau, n, nbw, nev, q, ldq, (cudaStream_t)stream);
+  return band_to_full_split_impl(a, lda, tau, n, nbw, nev, q, ldq, 0, -1, (cudaStream_t)stream);
+}
+extern "C" tbbt_status tbbt_trans_ev_band_to_full_split_opts_d(const double *a, int64_t lda, const double *tau,
+                                                               int64_t n, int64_t nbw, int64_t nev, double *q,
+                                                               int64_t ldq, int32_t wait_timeout_ms,
+                                                               int32_t debug_withhold_cta, void *stream) {
+  return band_to_full_split_impl(a, lda, tau, n, nbw, nev, q, ldq, wait_timeout_ms, debug_withhold_cta,
+                                 (cudaStream_t)stream);
 }

@@ -147,6 +147,11 @@ def test_band_to_full_argument_checks(L):
     odd = ctypes.c_void_p(ctypes.addressof(buf) + 4)
     assert L.tbbt_trans_ev_band_to_full_d(p, 10, p, 10, 4, 5, odd, 10, None) == EINVAL  # misaligned q
     assert L.tbbt_trans_ev_band_to_full_split_d(p, 10, p, 10, 4, 5, odd, 10, None) == EINVAL
+    f = L.tbbt_trans_ev_band_to_full_split_opts_d
+    assert f(p, 10, p, 10, 4, 5, p, 10, -1, -1, None) == EINVAL  # negative wait limit
+    assert f(p, 10, p, 10, 4, 5, p, 10, 0, -2, None) == EINVAL  # withhold index below -1
+    assert f(p, 10, p, 10, 0, 5, p, 10, 0, -1, None) == EINVAL  # nbw < 1
+    assert f(None, 10, None, 10, 10, 5, None, 10, 0, -1, None) == 0  # nbw >= n: nothing to do
 
 
 def test_bulge_chase_shape_limits_on_the_host(L):

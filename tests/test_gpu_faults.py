@@ -78,3 +78,26 @@ def test_withheld_progress_times_out_tcgen05_split(P):
     Zo = oracle.back_transform(v, tau, n, b, X.copy(order="F"))
     assert np.abs(q.cpu().numpy() - Zo).max() <= 1e-11
     good.close()
+
+
+def test_withheld_w_publication_times_out_split_band_to_full(P):
+    # the split band -> full form: CTA 1 (strip 0, slot 1) publishes its
+    # partial W but is never counted in, so the slots of strip 0 give up
+    # after 300 ms; every CTA drains its copies and products, frees its
+    # tensor memory and exits, and the next call computes correctly
+    n, b, nev = 600, 64, 300  # 3 strips of 128 columns, 8 slots each
+    a, tau = I.synthetic_full_store(n, b, 21, False)
+    Y = I.eigvec_block(n, nev, 22, False)
+    da = torch.from_numpy(np.ascontiguousarray(a.T)).cuda().t()
+    dt = torch.from_numpy(tau).cuda()
+    q = torch.from_numpy(np.ascontiguousarray(Y.T)).cuda().t()
+    P.trans_ev_band_to_full(da, dt, n, b, nev, q, variant=2, wait_timeout_ms=300, debug_withhold_cta=1)
+    with pytest.raises(P.TbbtError) as ei:
+        P.stream_check()
+    assert ei.value.status == 4  # TBBT_ETIMEOUT
+    P.stream_check()  # the error word was cleared
+    q = torch.from_numpy(np.ascontiguousarray(Y.T)).cuda().t()
+    P.trans_ev_band_to_full(da, dt, n, b, nev, q, variant=2)
+    P.stream_check()
+    Co = oracle.back_transform_full(a, tau, n, b, np.asfortranarray(Y.copy()), nthreads=8)
+    assert np.abs(q.cpu().numpy() - Co).max() <= 1e-11
