@@ -188,38 +188,83 @@ constexpr int SM_KMX = SM_U + 2 * D::UBYTES;
 constexpr int SM_BYTES = SM_KMX + 2 * D::NSUB * WS * 8 + 1024;  // + room to align the base to 1024 bytes
 static_assert(SM_BYTES <= 227 * 1024, "shared memory of the split band -> full kernel");
 
-// 16 rows of one column from the fixed-point Y (16-byte pairs; rows >= n and
-// invalid tiles read as zero), plus `add`
-__device__ __forceinline__ void load_rows16(const int64_t *zc, int32_t rb, int32_t n, bool valid, int64_t add,
-                                            int64_t (&z)[16]) {
+// The fixed-point Y is row-major (row r of the strip's 128 columns is 1 KB
+// of consecutive memory), so that the 32 lanes of a warp, which hold 32
+// consecutive columns, read and write 256 consecutive bytes per row. (With
+// the caller's column-major layout every lane would touch its own cache
+// line on each access.)
+// 16 rows of one column (rows >= n and invalid tiles read as zero), plus `add`
+__device__ __forceinline__ void load_rows16(const int64_t *zc, int64_t ldc, int32_t rb, int32_t n, bool valid,
+                                            int64_t add, int64_t (&z)[16]) {
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int32_t r = rb + 2 * i;
-    if (valid && r + 1 < n) {
-      const longlong2 v = __ldcg(reinterpret_cast<const longlong2 *>(zc + r));
-      z[2 * i] = v.x + add;
-      z[2 * i + 1] = v.y + add;
-    } else if (valid && r < n) {
-      z[2 * i] = (int64_t)__ldcg((const long long *)(zc + r)) + add;
-      z[2 * i + 1] = add;
-    } else {
-      z[2 * i] = add;
-      z[2 * i + 1] = add;
-    }
+  for (int i = 0; i < 16; ++i) {
+    const int32_t r = rb + i;
+    z[i] = (valid && r < n) ? (int64_t)__ldcg((const long long *)(zc + (int64_t)r * ldc)) + add : add;
   }
 }
-__device__ __forceinline__ void store_rows16(int64_t *zc, int32_t rb, int32_t n, const int64_t (&z)[16]) {
+__device__ __forceinline__ void store_rows16(int64_t *zc, int64_t ldc, int32_t rb, int32_t n, const int64_t (&z)[16]) {
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int32_t r = rb + 2 * i;
-    if (r + 1 < n) __stcg(reinterpret_cast<longlong2 *>(zc + r), make_longlong2(z[2 * i], z[2 * i + 1]));
-    else if (r < n) __stcg((long long *)(zc + r), (long long)z[2 * i]);
+  for (int i = 0; i < 16; ++i)
+    if (rb + i < n) __stcg((long long *)(zc + (int64_t)(rb + i) * ldc), (long long)z[i]);
+}
+
+// q (column-major, n x nev) <-> the row-major fixed-point Y: Z(r, c) =
+// round(q(r, c) 2^(FIX - e_c)), e_c the exponent of column c's norm (as
+// tcs::to_fixed_kernel). 32 x 32 tiles through shared memory, so that both
+// sides are read and written along their contiguous dimension.
+__global__ void __launch_bounds__(256) bfs_colexp_kernel(const double *__restrict__ q, int64_t ldq, int32_t n,
+                                                         int32_t nev, int32_t *__restrict__ col_exp) {
+  const int64_t c = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (c >= nev) return;
+  const double *col = q + c * ldq;
+  double ss = 0.0;
+  for (int32_t r = lane; r < n; r += 32) ss = fma(col[r], col[r], ss);
+  for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  int e = 0;
+  if (ss > 0.0) frexp(sqrt(ss), &e);
+  if (lane == 0) col_exp[c] = e;
+}
+__global__ void __launch_bounds__(256) bfs_to_fixed_kernel(const double *__restrict__ q, int64_t ldq,
+                                                           int64_t *__restrict__ z, int64_t ldc, int32_t n,
+                                                           int32_t nev, const int32_t *__restrict__ col_exp) {
+  __shared__ int64_t t[32][33];
+  const int32_t r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int32_t c = c0 + ty + 8 * j, r = r0 + tx;
+    if (c < nev && r < n) t[ty + 8 * j][tx] = __double2ll_rn(ldexp(q[(int64_t)c * ldq + r], FIX - col_exp[c]));
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int32_t r = r0 + ty + 8 * j, c = c0 + tx;
+    if (c < nev && r < n) z[(int64_t)r * ldc + c] = t[tx][ty + 8 * j];
+  }
+}
+__global__ void __launch_bounds__(256) bfs_from_fixed_kernel(double *__restrict__ q, int64_t ldq,
+                                                             const int64_t *__restrict__ z, int64_t ldc, int32_t n,
+                                                             int32_t nev, const int32_t *__restrict__ col_exp) {
+  __shared__ int64_t t[32][33];
+  const int32_t r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int32_t r = r0 + ty + 8 * j, c = c0 + tx;
+    if (c < nev && r < n) t[tx][ty + 8 * j] = z[(int64_t)r * ldc + c];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int32_t c = c0 + ty + 8 * j, r = r0 + tx;
+    if (c < nev && r < n) q[(int64_t)c * ldq + r] = ldexp(__ll2double_rn(t[ty + 8 * j][tx]), col_exp[c] - FIX);
   }
 }
 
 struct BfsArgs {
-  int64_t *z;  // fixed-point Y: column c, row r at c * ldz + r (16-byte aligned for even r; ldz even)
-  int64_t ldz;
+  int64_t *z;  // fixed-point Y, row-major: row r, column c at r * ldc + c
+  int64_t ldc;
   Layout L;
   int32_t nev, strips;
   const unsigned char *slices;   // items x BLOCK_BYTES
@@ -434,7 +479,7 @@ __global__ void __launch_bounds__(D::NTHREADS, 1) bfs_apply_kernel(BfsArgs a) {
         // --------------------------------------------------------------- math
         const int64_t C = kDigitOffset;
         const bool colok = c0 + col < a.nev;
-        int64_t *const zcol = a.z + (int64_t)(c0 + col) * a.ldz;
+        int64_t *const zcol = a.z + (c0 + col);
         const int sub = D::H * grp + hf;
         // reflector range of this thread set in the W readout (8 / 4 / 4 / 4 / 4 / 8)
         const int ca0 = sub == 0 ? 0 : (sub == 5 ? 24 : 4 + 4 * sub);
@@ -456,7 +501,7 @@ __global__ void __launch_bounds__(D::NTHREADS, 1) bfs_apply_kernel(BfsArgs a) {
         int64_t z[RT];
         if (nbat > 0) {
           const int32_t rb = my_row0(0);
-          load_rows16(zcol, rb, L.n, ok && rb >= 0 && colok, C, z);
+          load_rows16(zcol, a.ldc, rb, L.n, ok && rb >= 0 && colok, C, z);
         }
         for (int32_t bt = 0; bt < nbat; ++bt) {
           if (ok && n_batch > 0) {
@@ -514,7 +559,7 @@ __global__ void __launch_bounds__(D::NTHREADS, 1) bfs_apply_kernel(BfsArgs a) {
           }
           if (bt + 1 < nbat) {
             const int32_t rb = my_row0(bt + 1);
-            load_rows16(zcol, rb, L.n, ok && rb >= 0 && colok, C, z);
+            load_rows16(zcol, a.ldc, rb, L.n, ok && rb >= 0 && colok, C, z);
           }
           if (ok) ok = mbar_wait(&bars.g1, n_a & 1, &s_abort, a.err, a.timeout_ns);
           if (ok) {
@@ -621,7 +666,7 @@ __global__ void __launch_bounds__(D::NTHREADS, 1) bfs_apply_kernel(BfsArgs a) {
           // ---- pass C: corr of my rows, Z -= sum_l B_l 2^(rs + gu[r] - 8 l)
           for (int32_t bt = 0; bt < nbat && ok; ++bt) {
             const int32_t rb = my_row0(bt);
-            load_rows16(zcol, rb, L.n, rb >= 0 && colok, 0, z);
+            load_rows16(zcol, a.ldc, rb, L.n, rb >= 0 && colok, 0, z);
             uint32_t gu4[RT / 4];
             {
               const uint4 *gsrc = reinterpret_cast<const uint4 *>(items0 + (int64_t)bt * D::BLOCK_BYTES + D::VBYTES +
@@ -683,7 +728,7 @@ __global__ void __launch_bounds__(D::NTHREADS, 1) bfs_apply_kernel(BfsArgs a) {
             tc_fence_before();
             if (grp == 0) mbar_arrive(&bars.cfree);  // region A is free for part 2
             mbar_arrive(&bars.blk);
-            if (rb >= 0 && colok) store_rows16(zcol, rb, L.n, z);
+            if (rb >= 0 && colok) store_rows16(zcol, a.ldc, rb, L.n, z);
             ++n_c;
             ++n_batch;
           }

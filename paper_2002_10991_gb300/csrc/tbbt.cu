@@ -1330,6 +1330,7 @@ tbbt_status band_to_full_split_impl(const double *a, int64_t lda, const double *
   L.P = (int32_t)((K1 + bf::NB - 1) / bf::NB);
   L.ntiles = (int32_t)((n + 31) / 32);
   const int32_t strips = (int32_t)((nev + tcs::WS - 1) / tcs::WS);
+  if ((nev + 31) / 32 > 65535) return TBBT_ENOTSUP;  // grid of the layout transposes
   // S_K CTAs per strip, one CTA per SM: the fewest rounds of strips per CTA
   // group, each round taking about 1 / S_K of a strip's work (ties: fewer
   // slots, less exchange)
@@ -1354,7 +1355,7 @@ tbbt_status band_to_full_split_impl(const double *a, int64_t lda, const double *
       for (int32_t bt = 0; bt < nb; ++bt) items.push_back(bfs::Item{p, k, bt, 0});
       need[(size_t)p] += nb > 0;
     }
-  const int64_t ldz = (n + 3) & ~(int64_t)1;
+  const int64_t ldc = (int64_t)strips * tcs::WS;  // row length of the row-major fixed-point Y
   const int32_t grid = L.SK * std::min(strips, std::max(sms / L.SK, 1));  // <= sms
   // workspace (stream-ordered)
   const size_t b_T = round256(sizeof(double) * (size_t)L.P * bf::NB * bf::NB);
@@ -1363,7 +1364,7 @@ tbbt_status band_to_full_split_impl(const double *a, int64_t lda, const double *
   const size_t b_base = round256(sizeof(int32_t) * item_base.size());
   const size_t b_need = round256(sizeof(int32_t) * need.size());
   const size_t b_sl = round256((size_t)D::BLOCK_BYTES * items.size());
-  const size_t b_z = round256(sizeof(int64_t) * ((size_t)nev * (size_t)ldz + 2));
+  const size_t b_z = round256(sizeof(int64_t) * (size_t)n * (size_t)ldc);
   const size_t b_ce = round256(sizeof(int32_t) * (size_t)nev);
   const size_t b_wp = round256(sizeof(int64_t) * (size_t)strips * 2 * L.SK * bf::NB * tcs::WS);
   const size_t b_wc = round256(sizeof(unsigned) * (size_t)strips * L.P);
@@ -1392,8 +1393,7 @@ tbbt_status band_to_full_split_impl(const double *a, int64_t lda, const double *
             cudaSuccess ||
         cudaMemcpyAsync(d_need, need.data(), sizeof(int32_t) * need.size(), cudaMemcpyHostToDevice, s) !=
             cudaSuccess ||
-        cudaMemsetAsync(wcnt, 0, sizeof(unsigned) * (size_t)strips * L.P, s) != cudaSuccess ||
-        cudaMemsetAsync(zfix, 0, sizeof(int64_t) * ((size_t)nev * (size_t)ldz + 2), s) != cudaSuccess) {
+        cudaMemsetAsync(wcnt, 0, sizeof(unsigned) * (size_t)strips * L.P, s) != cudaSuccess) {
       rs = TBBT_ECUDA;
       break;
     }
@@ -1408,14 +1408,14 @@ tbbt_status band_to_full_split_impl(const double *a, int64_t lda, const double *
     bf::bf_tfactor_kernel<double><<<L.P, bf::THREADS, 0, s>>>(g, Tws, gv);
     bfs::bfs_prepare_kernel<<<(unsigned)items.size(), 128, 0, s>>>(g, L, d_items, Tws, gv, slices);
     const unsigned cblocks = (unsigned)((nev + 7) / 8);
-    // the conversions put row r of column c at zfix + 1 + c ldz + r + 1: even
-    // rows on 16-byte boundaries (ldz is even), as the apply kernel's pairs need
-    tcs::to_fixed_kernel<<<cblocks, 256, 0, s>>>(q, ldq, zfix + 1, ldz, (int32_t)n, (int32_t)nev, colexp);
+    const dim3 tgrid((unsigned)((n + 31) / 32), (unsigned)((nev + 31) / 32));
+    bfs::bfs_colexp_kernel<<<cblocks, 256, 0, s>>>(q, ldq, (int32_t)n, (int32_t)nev, colexp);
+    bfs::bfs_to_fixed_kernel<<<tgrid, 256, 0, s>>>(q, ldq, zfix, ldc, (int32_t)n, (int32_t)nev, colexp);
     if (cudaGetLastError() != cudaSuccess) { rs = TBBT_ECUDA; break; }
     if (allow_max_dynamic_smem(bfs::bfs_apply_kernel) != cudaSuccess) { rs = TBBT_ECUDA; break; }
     bfs::BfsArgs A;
-    A.z = zfix + 2;
-    A.ldz = ldz;
+    A.z = zfix;
+    A.ldc = ldc;
     A.L = L;
     A.nev = (int32_t)nev;
     A.strips = strips;
@@ -1438,7 +1438,7 @@ tbbt_status band_to_full_split_impl(const double *a, int64_t lda, const double *
       rs = TBBT_ECUDA;
       break;
     }
-    tcs::from_fixed_kernel<<<cblocks, 256, 0, s>>>(q, ldq, zfix + 1, ldz, (int32_t)n, (int32_t)nev, colexp);
+    bfs::bfs_from_fixed_kernel<<<tgrid, 256, 0, s>>>(q, ldq, zfix, ldc, (int32_t)n, (int32_t)nev, colexp);
     if (cudaGetLastError() != cudaSuccess) rs = TBBT_ECUDA;
   } while (0);
   cudaFreeAsync(ws, s);
