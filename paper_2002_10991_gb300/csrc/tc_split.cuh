@@ -590,6 +590,42 @@ __device__ __forceinline__ void w_levels(uint32_t taddr, int64_t *w) {
   }
 }
 
+// RT rows rb .. of one column of the fixed-point block (column pointer zc,
+// row r at zc[r]), as 16-byte pairs where the address allows (it does for
+// every window part: the parts start at odd rows, zc + r is then on a
+// 16-byte boundary), scalar otherwise; rows >= n are skipped / read as `add`.
+template <int RT>
+__device__ __forceinline__ void tc_store_rows(int64_t *zc, int32_t rb, int32_t n, const int64_t (&z)[RT], int64_t sub) {
+  const bool pairs = ((reinterpret_cast<uintptr_t>(zc + rb)) & 15) == 0;
+#pragma unroll
+  for (int i = 0; i < RT; i += 2) {
+    const int32_t r = rb + i;
+    if (pairs && r + 1 < n) {
+      *reinterpret_cast<longlong2 *>(zc + r) = make_longlong2(z[i] - sub, z[i + 1] - sub);
+    } else {
+      if (r < n) zc[r] = z[i] - sub;
+      if (r + 1 < n) zc[r + 1] = z[i + 1] - sub;
+    }
+  }
+}
+template <int RT>
+__device__ __forceinline__ void tc_load_rows(const int64_t *zc, int32_t rb, int32_t n, bool valid, int64_t add,
+                                             int64_t (&z)[RT]) {
+  const bool pairs = ((reinterpret_cast<uintptr_t>(zc + rb)) & 15) == 0;
+#pragma unroll
+  for (int i = 0; i < RT; i += 2) {
+    const int32_t r = rb + i;
+    if (valid && pairs && r + 1 < n) {
+      const longlong2 v = __ldcg(reinterpret_cast<const longlong2 *>(zc + r));
+      z[i] = v.x + add;
+      z[i + 1] = v.y + add;
+    } else {
+      z[i] = (valid && r < n) ? (int64_t)__ldcg((const long long *)(zc + r)) + add : add;
+      z[i + 1] = (valid && r + 1 < n) ? (int64_t)__ldcg((const long long *)(zc + r + 1)) + add : add;
+    }
+  }
+}
+
 struct TcBarriers {
   uint64_t zfull[S], blk, g1, wfull, c[3], cfree, v, u, stage, drain;
 };
@@ -788,14 +824,7 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
         const bool colok = c0 + col < a.nev;
         const int64_t *zcol = a.z + (int64_t)(c0 + col) * a.ldz + 1;
         int64_t z[RT];  // rows RT * hf .. of my part of the window, offset form
-        {
-          const int32_t rb = r0_of(0) + 32 * grp + RT * hf;
-#pragma unroll
-          for (int i = 0; i < RT; ++i) {
-            const int32_t r = rb + i;
-            z[i] = (colok && r < g.n) ? (int64_t)__ldcg((const long long *)(zcol + r)) + C : C;
-          }
-        }
+        tc_load_rows<RT>(zcol, r0_of(0) + 32 * grp + RT * hf, g.n, colok, C, z);
         // reflector range of this thread set in the W readout
         const int sub = D::H * grp + hf;
         int ca0, cw0, ca1, cw1;
@@ -1018,12 +1047,7 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
           // ---- the part leaving the window: store it, take the new rows
           if (t + 1 < nblk && p == P - 1) {
             const int32_t rb = r0 + 32 * (P - 1) + RT * hf;
-            if (colok) {
-              int64_t *dst = a.z + (int64_t)(c0 + col) * a.ldz + 1;
-#pragma unroll
-              for (int i = 0; i < RT; ++i)
-                if (rb + i < g.n) dst[rb + i] = z[i] - C;
-            }
+            if (colok) tc_store_rows<RT>(a.z + (int64_t)(c0 + col) * a.ldz + 1, rb, g.n, z, C);
             named_sync(2 + grp, 128 * D::H);  // then one release publishes the group's stores
             if ((warp & 3) == 0 && hf == 0 && lane == 0 && publish) st_release(myflag, rb);
             if (!mbar_wait(&bars.stage, n_st & 1, &s_abort, a.err, a.timeout_ns)) break;
@@ -1043,12 +1067,7 @@ __global__ void __launch_bounds__(Geo<B>::NTHREADS, 1) tc_apply_kernel(TcArgs a,
         if (!s_abort) {
           // the whole last window is final
           const int32_t rb = r0_of(nblk - 1) + 32 * ((grp + nblk - 1) % P) + RT * hf;
-          if (colok) {
-            int64_t *dst = a.z + (int64_t)(c0 + col) * a.ldz + 1;
-#pragma unroll
-            for (int i = 0; i < RT; ++i)
-              if (rb + i < g.n) dst[rb + i] = z[i] - C;
-          }
+          if (colok) tc_store_rows<RT>(a.z + (int64_t)(c0 + col) * a.ldz + 1, rb, g.n, z, C);
         }
       }
     }
