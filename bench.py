@@ -232,7 +232,7 @@ def b2f_bench(args):
         "cpu_baseline": {"value": cpu_tf, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
                          "sample": f"{ncs} of {nev} columns"},
         "parity": {"max_abs_err_vs_oracle": err, "columns": len(cols)},
-        "gpu_launches": (2 if args.variant == "fp64" else 6) * args.steps, "clocks": clocks.summary(),
+        "gpu_launches": (2 if args.variant == "fp64" else 7) * args.steps, "clocks": clocks.summary(),
         "variant": args.variant,
     }
     print(json.dumps(line), flush=True)

@@ -104,11 +104,9 @@ __device__ __forceinline__ T vget(const Geo &g, int32_t r, int32_t p, int32_t t)
 // T factor of every block (one thread block each): G = V^H V over the
 // block's rows, then T_kk = tau_k, T[0:k, k] = -tau_k T[0:k, 0:k] G[0:k, k]
 // (the forward recurrence of the WY representation). Tws: P x NB x NB,
-// column-major per block. With gvs (real data), also the block's scale
-// exponent for the split form: gvs[p] = e with every reflector norm
-// sqrt(G_kk) below 2^e (a margin of 2^-40 covers the rounding of G_kk).
+// column-major per block.
 template <typename T>
-__global__ void __launch_bounds__(THREADS) bf_tfactor_kernel(Geo g, T *__restrict__ Tws, int32_t *gvs = nullptr) {
+__global__ void __launch_bounds__(THREADS) bf_tfactor_kernel(Geo g, T *__restrict__ Tws) {
   constexpr int RC = sizeof(T) == 16 ? 32 : 64;  // static shared memory stays below 48 KB
   __shared__ T Vs[RC][PADT];
   __shared__ T Gs[NB][PADT];
@@ -138,15 +136,6 @@ __global__ void __launch_bounds__(THREADS) bf_tfactor_kernel(Geo g, T *__restric
 #pragma unroll
   for (int i = 0; i < 4; ++i) Gs[k][l0 + 8 * i] = acc[i];  // G[k][l] = v_k^H v_l
   __syncthreads();
-  if constexpr (sizeof(T) == 8) {
-    if (gvs && tid < NB) {
-      double mx = sqrt(fmax((double)Gs[tid][tid], 0.0));
-      for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      int e = 0;
-      if (mx > 0.0) frexp(mx * (1.0 + 0x1p-40), &e);
-      if (tid == 0) gvs[p] = e;
-    }
-  }
   if (tid < NB) {
     const int i = tid;
     const T *tau = reinterpret_cast<const T *>(g.tau);

@@ -69,9 +69,89 @@ __host__ __device__ inline int32_t slot_batches(const Layout &L, int32_t p, int3
   return (slot_count(L, p, k) + 2) / 3;
 }
 
-// gv[p] (from bf_tfactor_kernel): every reflector of block p has norm below
-// 2^gv, so V' = V 2^(60 - gv) has every entry, and by Cauchy-Schwarz every
-// partial W, in range.
+// T factors, balanced over the SMs. The Gram matrix G = V^T V of WY block p
+// runs over rows 32 p + b .. n - 1; on one thread block (as in b2f.cuh) the
+// first blocks' 32 x 32 x n FP64 products would each hold one SM's FP64 pipe
+// for the whole step. Here every chunk of GCH rows of a block is a thread
+// block of its own that writes its partial G to its own slot, and
+// bfs_tfactor_kernel sums a block's partials in chunk order (so the result
+// does not depend on scheduling), then runs the forward recurrence of the WY
+// representation: T_kk = tau_k, T[0:k, k] = -tau_k T[0:k, 0:k] G[0:k, k].
+// It also gives gv[p]: every reflector of block p has norm sqrt(G_kk) below
+// 2^gv (a margin of 2^-40 covers the rounding of G_kk), so V' = V 2^(60 - gv)
+// has every entry, and by Cauchy-Schwarz every partial W, in range.
+constexpr int GCH = 512;  // rows per Gram chunk
+
+__global__ void __launch_bounds__(256) bfs_gram_kernel(bf::Geo g, const int2 *__restrict__ pieces,
+                                                       double *__restrict__ gpart) {
+  constexpr int RC = 64;
+  __shared__ double Vs[RC][NB + 1];
+  const int2 pc = pieces[blockIdx.x];  // (block p, first row)
+  const int p = pc.x, tid = threadIdx.x;
+  const int k = tid % NB, l0 = tid / NB;  // owns G[k][l0 + 8 i]
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const int32_t rend = min(pc.y + GCH, g.n);
+  for (int32_t r0 = pc.y; r0 < rend; r0 += RC) {
+#pragma unroll
+    for (int i = 0; i < RC * NB / 256; ++i) {
+      const int e = tid + 256 * i;
+      const int r = e % RC, t = e / RC;
+      Vs[r][t] = r0 + r < rend ? bf::vget<double>(g, r0 + r, p, t) : 0.0;
+    }
+    __syncthreads();
+    for (int r = 0; r < RC; ++r) {
+      const double vk = Vs[r][k];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[i] = fma(vk, Vs[r][l0 + 8 * i], acc[i]);
+    }
+    __syncthreads();
+  }
+  double *out = gpart + (int64_t)blockIdx.x * NB * NB;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) out[k * NB + l0 + 8 * i] = acc[i];
+}
+
+__global__ void __launch_bounds__(256) bfs_tfactor_kernel(bf::Geo g, const double *__restrict__ gpart,
+                                                          const int32_t *__restrict__ chunk_base,
+                                                          double *__restrict__ Tws, int32_t *__restrict__ gvs) {
+  __shared__ double Gs[NB][NB + 1];
+  __shared__ double Ts[NB][NB + 1];
+  const int p = blockIdx.x, tid = threadIdx.x;
+  const int k = tid % NB, l0 = tid / NB;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int32_t j = chunk_base[p]; j < chunk_base[p + 1]; ++j) {
+    const double *src = gpart + (int64_t)j * NB * NB + k * NB + l0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[i] += src[8 * i];
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) Gs[k][l0 + 8 * i] = acc[i];
+  __syncthreads();
+  if (tid < NB) {
+    double mx = sqrt(fmax(Gs[tid][tid], 0.0));
+    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int e = 0;
+    if (mx > 0.0) frexp(mx * (1.0 + 0x1p-40), &e);
+    if (tid == 0) gvs[p] = e;
+    const int i = tid;
+    const double *tau = reinterpret_cast<const double *>(g.tau);
+    for (int kk = 0; kk < NB; ++kk) {
+      const int32_t c = NB * p + kk;
+      const double tk = c < g.K1 ? tau[c] : 0.0;
+      double val = 0.0;
+      if (i < kk) {
+        double sum = 0.0;
+        for (int l = i; l < kk; ++l) sum = fma(Ts[i][l], Gs[l][kk], sum);
+        val = -(tk * sum);
+      } else if (i == kk) {
+        val = tk;
+      }
+      Ts[i][kk] = val;
+      __syncwarp();
+    }
+    for (int kk = 0; kk < NB; ++kk) Tws[(int64_t)p * NB * NB + i + NB * kk] = Ts[i][kk];
+  }
+}
 
 // The digit slices of one (block, slot, batch): V' (96 rows x 32 reflectors,
 // K-major for GEMM1's B operand) and U' = (V T)' (three 32-row parts for
@@ -614,15 +694,27 @@ __global__ void __launch_bounds__(D::NTHREADS, 1) bfs_apply_kernel(BfsArgs a) {
           ok = ok && !s_abort;
           // ---- the block's W: sum of the partials, normalised per column,
           // split into digits -> the A operand of GEMM2 (as tc_split.cuh)
+          // slots with rows in this block: tile t0 .. ntiles - 1 belongs to slot t mod S_K
+          const int32_t t0b = first_tile_of(L, p);
+          unsigned act = 0;
+          for (int kk = 0; kk < SK; ++kk)
+            if ((((kk - t0b) % SK) + SK) % SK < L.ntiles - t0b) act |= 1u << kk;
           int64_t w[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) w[i] = 0;
+          if (ok) {
+#pragma unroll 1
+            for (int kk = 0; kk < SK; ++kk)
+              if ((act >> kk) & 1u) {
+                const int64_t *src = wp + ((int64_t)kk * NB + ca0) * WS + col;
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                  if (i < cw0) w[i] += (int64_t)__ldcg((const long long *)(src + (int64_t)i * WS));
+              }
+          }
           uint64_t mx = 0;
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            w[i] = 0;
-            if (ok && i < cw0)
-              for (int kk = 0; kk < SK; ++kk)
-                if (slot_batches(L, p, kk) > 0)
-                  w[i] += (int64_t)__ldcg((const long long *)(wp + ((int64_t)kk * NB + ca0 + i) * WS + col));
             const uint64_t ax = (uint64_t)(w[i] < 0 ? -w[i] : w[i]);
             mx = ax > mx ? ax : mx;
           }

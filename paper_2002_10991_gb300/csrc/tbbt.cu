@@ -1356,6 +1356,13 @@ tbbt_status band_to_full_split_impl(const double *a, int64_t lda, const double *
       need[(size_t)p] += nb > 0;
     }
   const int64_t ldc = (int64_t)strips * tcs::WS;  // row length of the row-major fixed-point Y
+  // Gram chunks of the T factors: GCH rows each, block after block
+  std::vector<int2> pieces;
+  std::vector<int32_t> chunk_base((size_t)L.P + 1, 0);
+  for (int32_t p = 0; p < L.P; ++p) {
+    for (int64_t r = 32 * (int64_t)p + L.b; r < n; r += bfs::GCH) pieces.push_back(make_int2(p, (int32_t)r));
+    chunk_base[(size_t)p + 1] = (int32_t)pieces.size();
+  }
   const int32_t grid = L.SK * std::min(strips, std::max(sms / L.SK, 1));  // <= sms
   // workspace (stream-ordered)
   const size_t b_T = round256(sizeof(double) * (size_t)L.P * bf::NB * bf::NB);
@@ -1368,7 +1375,10 @@ tbbt_status band_to_full_split_impl(const double *a, int64_t lda, const double *
   const size_t b_ce = round256(sizeof(int32_t) * (size_t)nev);
   const size_t b_wp = round256(sizeof(int64_t) * (size_t)strips * 2 * L.SK * bf::NB * tcs::WS);
   const size_t b_wc = round256(sizeof(unsigned) * (size_t)strips * L.P);
-  const size_t total = b_T + b_gv + b_items + b_base + b_need + b_sl + b_z + b_ce + b_wp + b_wc;
+  const size_t b_pc = round256(sizeof(int2) * pieces.size());
+  const size_t b_cb = round256(sizeof(int32_t) * chunk_base.size());
+  const size_t b_gp = round256(sizeof(double) * pieces.size() * bf::NB * bf::NB);
+  const size_t total = b_T + b_gv + b_items + b_base + b_need + b_sl + b_z + b_ce + b_wp + b_wc + b_pc + b_cb + b_gp;
   unsigned char *ws = nullptr;
   TBBT_CUDA_TRY(cudaMallocAsync((void **)&ws, total, s));
   tbbt_status rs = TBBT_OK;
@@ -1383,7 +1393,10 @@ tbbt_status band_to_full_split_impl(const double *a, int64_t lda, const double *
     int64_t *zfix = (int64_t *)p0; p0 += b_z;
     int32_t *colexp = (int32_t *)p0; p0 += b_ce;
     int64_t *wpart = (int64_t *)p0; p0 += b_wp;
-    unsigned *wcnt = (unsigned *)p0;
+    unsigned *wcnt = (unsigned *)p0; p0 += b_wc;
+    int2 *d_pieces = (int2 *)p0; p0 += b_pc;
+    int32_t *d_cbase = (int32_t *)p0; p0 += b_cb;
+    double *gpart = (double *)p0;
     // the host vectors live until the end of this call: the copies below are
     // ordered on s before any kernel that reads them, and are from pageable
     // memory, which the runtime stages before returning
@@ -1393,6 +1406,10 @@ tbbt_status band_to_full_split_impl(const double *a, int64_t lda, const double *
             cudaSuccess ||
         cudaMemcpyAsync(d_need, need.data(), sizeof(int32_t) * need.size(), cudaMemcpyHostToDevice, s) !=
             cudaSuccess ||
+        cudaMemcpyAsync(d_pieces, pieces.data(), sizeof(int2) * pieces.size(), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(d_cbase, chunk_base.data(), sizeof(int32_t) * chunk_base.size(), cudaMemcpyHostToDevice,
+                        s) != cudaSuccess ||
         cudaMemsetAsync(wcnt, 0, sizeof(unsigned) * (size_t)strips * L.P, s) != cudaSuccess) {
       rs = TBBT_ECUDA;
       break;
@@ -1405,7 +1422,8 @@ tbbt_status band_to_full_split_impl(const double *a, int64_t lda, const double *
     g.b = L.b;
     g.K1 = (int32_t)K1;
     g.P = L.P;
-    bf::bf_tfactor_kernel<double><<<L.P, bf::THREADS, 0, s>>>(g, Tws, gv);
+    bfs::bfs_gram_kernel<<<(unsigned)pieces.size(), 256, 0, s>>>(g, d_pieces, gpart);
+    bfs::bfs_tfactor_kernel<<<L.P, 256, 0, s>>>(g, gpart, d_cbase, Tws, gv);
     bfs::bfs_prepare_kernel<<<(unsigned)items.size(), 128, 0, s>>>(g, L, d_items, Tws, gv, slices);
     const unsigned cblocks = (unsigned)((nev + 7) / 8);
     const dim3 tgrid((unsigned)((n + 31) / 32), (unsigned)((nev + 31) / 32));
