@@ -408,6 +408,18 @@ tbbt_status tbbt_fp64_probe(int32_t kind, int32_t blocks, int32_t threads, int64
 int64_t tbbt_schedule_max_live_rows(int64_t n, int64_t nbw, int is_complex, int32_t sweeps_per_block,
                                     int32_t stages_per_step);
 
+/* Host-side check of the split band -> full form's layout (no GPU needed):
+ * for these sizes and an SM count, walks the layout the launcher of
+ * tbbt_trans_ev_band_to_full_split_d would use, as its kernels walk it, and
+ * returns 0 if every row of every 32-reflector block belongs to exactly one
+ * (slot, batch, part) row of both the apply and the preparation kernel, each
+ * (strip, slot) has exactly one CTA, and each block's counter target is its
+ * number of slots with rows; a negative code names the first failed check
+ * (-1: bad arguments). *slots_per_strip and *items (nullable) receive the
+ * slots per 128-column strip and the number of (block, slot, batch) items. */
+int64_t tbbt_b2f_split_layout_check(int64_t n, int64_t nbw, int64_t nev, int32_t sms, int32_t *slots_per_strip,
+                                    int64_t *items);
+
 #ifdef __cplusplus
 }
 #endif

@@ -107,6 +107,8 @@ def load():
         L.tbbt_tridiag_eig.argtypes = [p, p, i64, i64, p, p, i64, c_int, p]
         L.tbbt_fp64_probe.restype = c_int
         L.tbbt_fp64_probe.argtypes = [i32, i32, i32, i64, p, ctypes.POINTER(ctypes.c_double), p]
+        L.tbbt_b2f_split_layout_check.restype = i64
+        L.tbbt_b2f_split_layout_check.argtypes = [i64, i64, i64, i32, ctypes.POINTER(i32), ctypes.POINTER(i64)]
         L.tbbt_schedule_max_live_rows.restype = i64
         L.tbbt_schedule_max_live_rows.argtypes = [i64, i64, c_int, i32, i32]
         _lib = L

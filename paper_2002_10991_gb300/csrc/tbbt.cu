@@ -1303,6 +1303,51 @@ extern "C" tbbt_status tbbt_tridiag_eig(const double *d, const double *e, int64_
 // Band -> full back-transformation (Eq. 6e), split-precision form on tcgen05
 // ---------------------------------------------------------------------------
 namespace {
+// Host side of the split form's layout: S_K, the (block, slot, batch) items
+// in the order the slices are laid out, each (block, slot)'s first item, and
+// per block the number of slots with rows (the target of its W counter).
+struct BfsPlan {
+  tbbt::bfs::Layout L;
+  int32_t strips = 0, grid = 0;
+  std::vector<tbbt::bfs::Item> items;
+  std::vector<int32_t> item_base, need;
+};
+void bfs_make_plan(int64_t n, int64_t nbw, int64_t nev, int32_t sms, BfsPlan &pl) {
+  namespace bfs = tbbt::bfs;
+  bfs::Layout &L = pl.L;
+  const int64_t K1 = n > nbw ? n - nbw : 0;
+  L.n = (int32_t)n;
+  L.b = (int32_t)std::min<int64_t>(nbw, n);
+  L.K1 = (int32_t)K1;
+  L.P = (int32_t)((K1 + tbbt::bf::NB - 1) / tbbt::bf::NB);
+  L.ntiles = (int32_t)((n + 31) / 32);
+  pl.strips = (int32_t)((nev + tbbt::tcs::WS - 1) / tbbt::tcs::WS);
+  // S_K CTAs per strip, one CTA per SM: the fewest rounds of strips per CTA
+  // group, each round taking about 1 / S_K of a strip's work (ties: fewer
+  // slots, less exchange)
+  double best = 0.0;
+  L.SK = 1;
+  for (int32_t sk = 1; sk <= 8 && sk <= sms; ++sk) {
+    const int32_t conc = std::max(sms / sk, 1);
+    const double t = (double)((pl.strips + conc - 1) / conc) / sk;
+    if (sk == 1 || t < best * 0.999) {
+      best = t;
+      L.SK = sk;
+    }
+  }
+  pl.grid = L.SK * std::min(pl.strips, std::max(sms / L.SK, 1));  // <= sms
+  pl.items.clear();
+  pl.item_base.assign((size_t)L.P * L.SK, 0);
+  pl.need.assign((size_t)L.P, 0);
+  for (int32_t p = 0; p < L.P; ++p)
+    for (int32_t k = 0; k < L.SK; ++k) {
+      pl.item_base[(size_t)p * L.SK + k] = (int32_t)pl.items.size();
+      const int32_t nb = bfs::slot_batches(L, p, k);
+      for (int32_t bt = 0; bt < nb; ++bt) pl.items.push_back(bfs::Item{p, k, bt, 0});
+      pl.need[(size_t)p] += nb > 0;
+    }
+}
+
 tbbt_status band_to_full_split_impl(const double *a, int64_t lda, const double *tau, int64_t n, int64_t nbw,
                                     int64_t nev, double *q, int64_t ldq, int32_t wait_timeout_ms,
                                     int32_t debug_withhold_cta, cudaStream_t s) {
@@ -1323,38 +1368,13 @@ tbbt_status band_to_full_split_impl(const double *a, int64_t lda, const double *
   if (major != 10) return TBBT_ENOTSUP;
   TBBT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   // layout: 32-reflector blocks, 32-row tiles dealt to S_K slots per 128-column strip
-  bfs::Layout L;
-  L.n = (int32_t)n;
-  L.b = (int32_t)std::min<int64_t>(nbw, n);
-  L.K1 = (int32_t)K1;
-  L.P = (int32_t)((K1 + bf::NB - 1) / bf::NB);
-  L.ntiles = (int32_t)((n + 31) / 32);
-  const int32_t strips = (int32_t)((nev + tcs::WS - 1) / tcs::WS);
   if ((nev + 31) / 32 > 65535) return TBBT_ENOTSUP;  // grid of the layout transposes
-  // S_K CTAs per strip, one CTA per SM: the fewest rounds of strips per CTA
-  // group, each round taking about 1 / S_K of a strip's work (ties: fewer
-  // slots, less exchange)
-  {
-    double best = 0.0;
-    L.SK = 1;
-    for (int32_t sk = 1; sk <= 8 && sk <= sms; ++sk) {
-      const int32_t conc = std::max(sms / sk, 1);
-      const double t = (double)((strips + conc - 1) / conc) / sk;
-      if (sk == 1 || t < best * 0.999) {
-        best = t;
-        L.SK = sk;
-      }
-    }
-  }
-  std::vector<bfs::Item> items;
-  std::vector<int32_t> item_base((size_t)L.P * L.SK), need((size_t)L.P, 0);
-  for (int32_t p = 0; p < L.P; ++p)
-    for (int32_t k = 0; k < L.SK; ++k) {
-      item_base[(size_t)p * L.SK + k] = (int32_t)items.size();
-      const int32_t nb = bfs::slot_batches(L, p, k);
-      for (int32_t bt = 0; bt < nb; ++bt) items.push_back(bfs::Item{p, k, bt, 0});
-      need[(size_t)p] += nb > 0;
-    }
+  BfsPlan pl;
+  bfs_make_plan(n, nbw, nev, sms, pl);
+  const bfs::Layout &L = pl.L;
+  const int32_t strips = pl.strips, grid = pl.grid;
+  const std::vector<bfs::Item> &items = pl.items;
+  const std::vector<int32_t> &item_base = pl.item_base, &need = pl.need;
   const int64_t ldc = (int64_t)strips * tcs::WS;  // row length of the row-major fixed-point Y
   // Gram chunks of the T factors: GCH rows each, block after block
   std::vector<int2> pieces;
@@ -1363,7 +1383,6 @@ tbbt_status band_to_full_split_impl(const double *a, int64_t lda, const double *
     for (int64_t r = 32 * (int64_t)p + L.b; r < n; r += bfs::GCH) pieces.push_back(make_int2(p, (int32_t)r));
     chunk_base[(size_t)p + 1] = (int32_t)pieces.size();
   }
-  const int32_t grid = L.SK * std::min(strips, std::max(sms / L.SK, 1));  // <= sms
   // workspace (stream-ordered)
   const size_t b_T = round256(sizeof(double) * (size_t)L.P * bf::NB * bf::NB);
   const size_t b_gv = round256(sizeof(int32_t) * (size_t)L.P);
@@ -1475,4 +1494,73 @@ extern "C" tbbt_status tbbt_trans_ev_band_to_full_split_opts_d(const double *a, 
                                                                int32_t debug_withhold_cta, void *stream) {
   return band_to_full_split_impl(a, lda, tau, n, nbw, nev, q, ldq, wait_timeout_ms, debug_withhold_cta,
                                  (cudaStream_t)stream);
+}
+
+// Host-side check of the split form's layout (no GPU needed): the layout the
+// launcher would use for these sizes and SM count, walked as the kernels walk
+// it. Returns 0 if every row of every WY block (rows 32 p + nbw .. n - 1)
+// belongs to exactly one (slot, batch, part, half, row) of the apply kernel,
+// the preparation kernel maps every item's rows the same way, the items and
+// their first indices agree, each block's counter target is its number of
+// slots with rows (which only grows from the last block to the first), the
+// in-kernel test of a slot's rows agrees with slot_batches, and every
+// (strip, slot) has one CTA; a negative code names the first check that
+// fails. *slots_per_strip and *items receive S_K and the item count.
+extern "C" int64_t tbbt_b2f_split_layout_check(int64_t n, int64_t nbw, int64_t nev, int32_t sms,
+                                              int32_t *slots_per_strip, int64_t *items_out) {
+  namespace bfs = tbbt::bfs;
+  if (n < 1 || nbw < 1 || nev < 1 || nev > n || sms < 1) return -1;
+  if (n <= nbw) return 0;
+  BfsPlan pl;
+  bfs_make_plan(n, nbw, nev, sms, pl);
+  const bfs::Layout &L = pl.L;
+  if (slots_per_strip) *slots_per_strip = L.SK;
+  if (items_out) *items_out = (int64_t)pl.items.size();
+  if (pl.grid > sms || pl.grid % L.SK) return -2;
+  // every (strip, slot) taken by exactly one CTA (blockIdx / S_K, stepping by grid / S_K)
+  std::vector<int32_t> owner((size_t)pl.strips * L.SK, 0);
+  for (int32_t bx = 0; bx < pl.grid; ++bx)
+    for (int32_t st = bx / L.SK; st < pl.strips; st += pl.grid / L.SK) ++owner[(size_t)st * L.SK + bx % L.SK];
+  for (int32_t c : owner)
+    if (c != 1) return -3;
+  std::vector<int32_t> seen((size_t)n);
+  int32_t prev_active = 0;
+  for (int32_t p = L.P - 1; p >= 0; --p) {
+    std::fill(seen.begin(), seen.end(), 0);
+    int32_t active = 0;
+    const int32_t t0 = bfs::first_tile_of(L, p);
+    for (int32_t k = 0; k < L.SK; ++k) {
+      const int32_t f = bfs::slot_first(L, p, k), cnt = bfs::slot_count(L, p, k), nb = bfs::slot_batches(L, p, k);
+      const bool has = ((((k - t0) % L.SK) + L.SK) % L.SK) < L.ntiles - t0;  // the apply kernel's mask
+      if (has != (nb > 0)) return -4;
+      active += nb > 0;
+      const int64_t ib = pl.item_base[(size_t)p * L.SK + k];
+      if (ib + nb > (int64_t)pl.items.size()) return -5;
+      for (int32_t bt = 0; bt < nb; ++bt) {
+        const bfs::Item &it = pl.items[(size_t)(ib + bt)];
+        if (it.p != p || it.k != k || it.beta != bt) return -6;
+        for (int32_t grp = 0; grp < 3; ++grp)
+          for (int32_t hf = 0; hf < 2; ++hf) {
+            const int32_t j = 3 * bt + grp;
+            const int32_t rb = j < cnt ? 32 * (f + j * L.SK) + 16 * hf : -1;  // the apply kernel's rows
+            for (int32_t i = 0; i < 16; ++i) {
+              const int32_t rr = 32 * grp + 16 * hf + i;  // the item's row (the preparation kernel's)
+              const int32_t jp = 3 * bt + rr / 32;
+              const int32_t row_prep = jp < cnt ? 32 * (f + jp * L.SK) + (rr & 31) : -1;
+              const int32_t row = rb >= 0 ? rb + i : -1;
+              if (row != row_prep) return -7;
+              if (row >= 0 && (row / 32) % L.SK != k) return -8;  // tile t belongs to slot t mod S_K
+              if (row >= 0 && row < n) ++seen[(size_t)row];
+            }
+          }
+      }
+    }
+    if (active != pl.need[(size_t)p] || active < prev_active) return -9;
+    prev_active = active;
+    for (int64_t r = 0; r < n; ++r) {
+      const bool in_block = r >= 32 * (int64_t)p + L.b;
+      if (seen[(size_t)r] > 1 || (in_block && seen[(size_t)r] != 1) || (r < 32 * (int64_t)t0 && seen[(size_t)r])) return -10;
+    }
+  }
+  return 0;
 }
