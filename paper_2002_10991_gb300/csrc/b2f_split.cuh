@@ -32,7 +32,10 @@
 //           subtracted from the rows, which go back to global memory.
 // The V' / U' digit slices of every (block, slot, batch) are prepared per
 // call in FP64 (T and U = V T) by bfs_prepare_kernel, in the operand layouts
-// of tc_split.cuh (96 K-rows of V', three 32-row parts of U').
+// of tc_split.cuh (96 K-rows of V', three 32-row parts of U'); the T factors
+// come from Gram matrices summed over 512-row chunks (bfs_gram_kernel,
+// bfs_tfactor_kernel). The fixed-point copy of Y is row-major, so that a
+// warp's 32 columns of one row are 256 consecutive bytes.
 #pragma once
 
 #include "b2f.cuh"
